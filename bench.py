@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the mQO hot path on GB300.
+
+Default workload (the batched MIS configuration): 512 Erdős–Rényi graphs,
+n ~ U[700, 800], p = 0.15, seeds 0..511, packed CSR, 32 trajectories per
+graph (16,384 trajectories), BF16 x / momentum state with FP32 arithmetic.
+A step is one tick of the full per-trajectory machine over all
+trajectories (fused SpMM-gradient step, projection, rounding, exact
+evaluation, acceptance, mutation resets, repair and local search).
+Metric: edge-updates/s = nnz * B per step / step time.
+
+Arms:
+  default            the CUDA library (one process per GPU, weak scaling)
+  --impl reference   the plain CPU oracle on the host cores, bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import mqo_inputs as mi  # noqa: E402
+
+METRIC = "edge-updates/s of fused mQO steps"
+UNIT = "edge-updates/s"
+L2_BYTES = 126 * 1024 * 1024
+
+WORKLOADS = {
+    "mis_batched": dict(desc="MIS batched: 512 ER graphs n~U[700,800] p=0.15 seeds 0..511, packed CSR, B=32 "
+                             "per graph (16384 trajectories)", problem=0, batch=32, alpha=0.8, momentum=0.45,
+                        gamma=2.0, rho=0.6, t_gs=60, descent_cap=50, init_kind=1, sigma=0.1),
+    "maxcut_regular": dict(desc="MaxCut f_B: random 3-regular n=100000, B=128", problem=1, batch=128, alpha=0.0025,
+                           momentum=0.8, lambda_=0.001, rho=0.8, t_gs=90, descent_cap=200, init_kind=1, sigma=0.1),
+    "mis_scale": dict(desc="MIS at scale: ER n=1e7 mean degree 10, B=16", problem=0, batch=16, alpha=0.8,
+                      momentum=0.75, gamma=2.0, rho=0.5, t_gs=60, descent_cap=50, init_kind=1, sigma=0.1),
+}
+
+
+def make_graph(name):
+    if name == "mis_batched":
+        return mi.workload_mis_batched()
+    if name == "maxcut_regular":
+        return mi.workload_maxcut_regular()
+    if name == "mis_scale":
+        return mi.workload_mis_scale()
+    raise ValueError(name)
+
+
+def dtype_code(s):
+    return {"f32": 0, "bf16": 1, "f16": 2}[s]
+
+
+# ---------------------------------------------------------------- CPU oracle (reference arm, cpu_baseline)
+def _oracle_job(args):
+    gi, rp, col, w, n, pdict, traj, ticks = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    G = mi.Graph(n, rp, col, w)
+    og = oracle.Graph(G)
+    p = oracle.params(**pdict)
+    tr = oracle.Trajectory(og, p, traj)
+    t0 = time.perf_counter()
+    tr.run(ticks)
+    return time.perf_counter() - t0, int(rp[-1]) * ticks, tr.state["best"]
+
+
+def oracle_sample(G, wl, x_dtype, v_dtype, target_s=12.0, cores=None):
+    """Time the oracle on a bounded sample of the workload's trajectories."""
+    cores = cores or os.cpu_count() or 1
+    pd = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
+                             "sigma") if k in wl}
+    pd.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), x_dtype=x_dtype, v_dtype=v_dtype,
+              seed=0)
+    B = wl["batch"]
+    # probe one trajectory to size the sample
+    sub = G.subgraph(0)
+    job = (0, sub.row_ptr, sub.col_idx, sub.weights, sub.n, pd, 0, 20)
+    dt, eu, _ = _oracle_job(job)
+    rate1 = eu / max(dt, 1e-9)
+    per_traj_eu = sub.nnz * 200
+    ticks = 200
+    ntraj = max(cores, int(target_s * rate1 * cores / per_traj_eu))
+    ntraj = min(ntraj, G.num_graphs * B, 4096)
+    jobs = []
+    for k in range(ntraj):
+        g = k % G.num_graphs
+        b = (k // G.num_graphs) % B
+        sg = G.subgraph(g)
+        jobs.append((g, sg.row_ptr, sg.col_idx, sg.weights, sg.n, pd, g * B + b, ticks))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    eu = sum(r[1] for r in res)
+    return dict(value=eu / wall, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{ntraj} trajectories x {ticks} ticks of the same workload (member graphs 0..), "
+                       f"{eu:.3e} edge-updates in {wall:.2f} s wall on {cores} processes")
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    G = make_graph(args.workload)
+    xd = dtype_code(args.x_dtype)
+    vd = dtype_code(args.v_dtype or args.x_dtype)
+    per_step = []
+    base = None
+    for _ in range(args.warmup):
+        oracle_sample(G, wl, xd, vd, target_s=0.5)
+    for _ in range(args.steps):
+        base = oracle_sample(G, wl, xd, vd, target_s=max(1.0, 60.0 / max(args.steps, 1)))
+        per_step.append(base["value"])
+    value = statistics.median(per_step)
+    nnz_b = G.nnz * wl["batch"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": nnz_b / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "x_dtype": args.x_dtype, "v_dtype": args.v_dtype or args.x_dtype,
+                   "nnz": G.nnz, "batch": wl["batch"]},
+        "cpu_baseline": dict(base, value=value),
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def algorithmic_bytes_per_step(G, B, sx, sv):
+    """col_idx + row_ptr read once, x read + written, momentum read + written,
+    rounding bits written (one word per node per 32 trajectories)."""
+    n = G.n
+    bw = (B + 31) // 32
+    return G.nnz * 4 + (n + 1) * 4 + 2 * n * B * sx + 2 * n * B * sv + n * bw * 4
+
+
+def step_kernel_traffic(workload, x_dtype):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    or None if the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}_{x_dtype}.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t:
+        return None
+    h = hashlib.sha256()
+    for f in ("mqo_step.cu", "mqo_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_06921_gb300", "csrc", f), "rb").read())
+    if h.hexdigest() != m.group(1):
+        return None
+    return float(t.group(1))
+
+
+def gpu_arm(args):
+    import torch
+    import paper_2605_06921_gb300 as mq
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    xd, vd = dtype_code(args.x_dtype), dtype_code(args.v_dtype or args.x_dtype)
+    sx, sv = (4 if xd == 0 else 2), (4 if vd == 0 else 2)
+    G = make_graph(args.workload)
+    B = wl["batch"]
+    pkw = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
+                              "sigma")}
+    pkw.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), seed=1000 * rank)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def measure(x_dtype, v_dtype, steps, warmup, sample_clocks):
+        g = mq.Graph(G)
+        s = mq.Solver(g, mq.params(x_dtype=x_dtype, v_dtype=v_dtype, **pkw))
+        s.run(warmup)
+        torch.cuda.synchronize()
+        barrier()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step_ms, launches = s.run_timed(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        if sampler:
+            sampler.__exit__()
+        ms = e0.elapsed_time(e1)
+        clocks = sampler.summary() if sampler else None
+        vals, _ = s.best(want_bits=False)
+        s.close()
+        g.close()
+        return ms, step_ms / max(launches, 1), clocks, vals
+
+    nnz_b = G.nnz * B
+    ms, step_avg_ms, clocks, best_vals = measure(xd, vd, args.steps, args.warmup, True)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = nnz_b * args.steps * world / (ms / 1e3)
+
+    # the plain FP32-state form of the same workload, for comparison
+    f32 = None
+    if xd != 0 and not args.no_compare:
+        ms32, step32, _, _ = measure(0, 0, max(1, args.steps // 2), args.warmup, False)
+        f32 = {"value": nnz_b * max(1, args.steps // 2) / (ms32 / 1e3), "ms_per_step": ms32 / max(1, args.steps // 2),
+               "step_kernel_ms": step32}
+
+    # end to end through the public API with host buffers: graph upload from
+    # host arrays, solver creation, every tick followed by a device->host
+    # read of the per-trajectory best values
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    g = mq.Graph(G)
+    s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **pkw))
+    e2e_steps = args.steps
+    for _ in range(e2e_steps):
+        s.run(1)
+        vals, _ = s.best(want_bits=False)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    s.close()
+    g.close()
+    t_t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+    t_e2e = float(t_t.item())
+    csr_bytes = G.nnz * 4 + (G.n + 1) * 8 + (G.nnz if G.weights is not None else 0) + 8 * (G.num_graphs + 1)
+    e2e = {"value": nnz_b * e2e_steps * world / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(csr_bytes / e2e_steps), "d2h_bytes_per_step": int(8 * G.num_graphs * B)}
+
+    alg = algorithmic_bytes_per_step(G, B, sx, sv)
+    achieved = alg / (step_avg_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": step_kernel_traffic(args.workload, args.x_dtype), "kernel": "mqo::k_step",
+            "step_kernel_ms": step_avg_ms, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(G, wl, xd, vd, target_s=12.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "x_dtype": args.x_dtype, "v_dtype": args.v_dtype or args.x_dtype,
+                       "nnz": G.nnz, "nodes": G.n, "batch": B, "edge_updates_per_step": nnz_b,
+                       "l2": "inputs larger than L2 (CSR + state > 126 MB)", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": 7 * args.steps,
+            "clocks": clocks, "best_mean": float(np.mean(best_vals)), "best_max": int(np.max(best_vals)),
+        }
+        if f32:
+            line["fp32_state"] = f32
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="mis_batched", choices=sorted(WORKLOADS))
+    ap.add_argument("--x-dtype", default="bf16", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--v-dtype", default=None, choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,814 @@
+// mqo_api.cu -- host runtime and C ABI of the mQO library (see include/mqo.h).
+//
+// Graphs are validated once on the host and deep-copied to device memory.
+// A solver owns all device state of its trajectories and an internal
+// non-blocking stream; every call is ordered after earlier work of the
+// caller's stream and before later work on it through a pair of events.
+// The machine's tick (control, apply, step, three discrete passes, tick
+// end) is captured once as a CUDA graph and replayed.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mqo.h"
+#include "mqo_host.h"
+
+using namespace mqo;
+
+namespace {
+
+thread_local std::string g_err;
+
+mqo_status fail(mqo_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+constexpr int kChunkNodes = 512;  // nodes per item
+constexpr int kSplit = 512;       // row length above which the f_B kernels chunk a row
+
+}  // namespace
+
+#define CKG(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail(MQO_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct mqo_graph_s {
+  int64_t n = 0, nnz = 0;
+  int32_t G = 0;
+  int32_t* d_rp = nullptr;
+  int32_t* d_col = nullptr;
+  int8_t* d_w = nullptr;
+  int32_t* d_off = nullptr;
+  int32_t* d_dmax = nullptr;
+  Item* d_items = nullptr;
+  int32_t num_items = 0;
+  std::vector<int32_t> h_rp;
+  // f_B kernels: chunk plan of long rows and their scratch
+  bool hp_built = false;
+  HeavyPlan hp{};
+  int32_t* d_hp = nullptr;
+  float* d_scratch = nullptr;
+  size_t scratch_floats = 0;
+  int sms = 152;
+
+  GraphDev dev() const {
+    GraphDev g;
+    g.n = (int32_t)n;
+    g.num_graphs = G;
+    g.nnz = nnz;
+    g.row_ptr = d_rp;
+    g.col = d_col;
+    g.w = d_w;
+    g.node_off = d_off;
+    g.dmax = d_dmax;
+    g.items = d_items;
+    g.num_items = num_items;
+    return g;
+  }
+};
+
+struct mqo_solver_s {
+  mqo_graph g = nullptr;
+  mqo_params p{};
+  SolverDev S{};
+  cudaStream_t user = nullptr;
+  cudaStream_t work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gx1 = nullptr, gx16 = nullptr;
+  bool poisoned = false;
+  int grid = 1;
+  int64_t host_tick = 0;
+  Counters* d_cnt_plain = nullptr;
+  uint32_t* d_zplain = nullptr;
+  Counters* d_eval = nullptr;
+  int32_t* h_pending = nullptr;  // pinned
+  int32_t* d_pending = nullptr;
+  // saved state around a standalone local search
+  void* d_save = nullptr;
+  std::vector<void*> allocs;
+  size_t x_bytes = 0, v_bytes = 0, words = 0, pairs = 0;
+};
+
+namespace {
+
+template <typename T>
+mqo_status dalloc(T** p, size_t count, std::vector<void*>* track) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(MQO_ENOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+  *p = static_cast<T*>(q);
+  if (track) track->push_back(q);
+  return MQO_OK;
+}
+
+size_t dtype_size(int d) { return d == DT_F32 ? 4 : 2; }
+
+// Host validation of symmetric CSR (see mqo_graph_create_csr).
+mqo_status validate(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col, const int8_t* w,
+                    const int64_t* offs, int32_t G) {
+  if (n < 1 || n >= (1LL << 31)) return fail(MQO_EINVAL, "n=%lld out of range [1, 2^31)", (long long)n);
+  if (nnz < 0 || nnz >= (1LL << 31)) return fail(MQO_EINVAL, "nnz=%lld out of range [0, 2^31)", (long long)nnz);
+  if (rp[0] != 0 || rp[n] != nnz) return fail(MQO_EGRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz");
+  for (int64_t v = 0; v < n; ++v)
+    if (rp[v + 1] < rp[v]) return fail(MQO_EGRAPH, "row_ptr decreases at row %lld", (long long)v);
+  std::vector<int32_t> graph_of;
+  if (offs) {
+    graph_of.resize((size_t)n);
+    for (int32_t g = 0; g < G; ++g)
+      for (int64_t v = offs[g]; v < offs[g + 1]; ++v) graph_of[(size_t)v] = g;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    for (int64_t j = rp[v]; j < rp[v + 1]; ++j) {
+      const int32_t u = col[j];
+      if (u < 0 || u >= n) return fail(MQO_EGRAPH, "col_idx[%lld]=%d out of range", (long long)j, u);
+      if (u == v) return fail(MQO_EGRAPH, "self loop at node %lld", (long long)v);
+      if (j > rp[v] && col[j - 1] >= u)
+        return fail(MQO_EGRAPH, "row %lld not strictly ascending at entry %lld", (long long)v, (long long)j);
+      if (w && w[j] != 1 && w[j] != -1) return fail(MQO_EGRAPH, "weight %d at entry %lld not in {-1,+1}", w[j], (long long)j);
+      if (offs && graph_of[(size_t)u] != graph_of[(size_t)v])
+        return fail(MQO_EGRAPH, "edge (%lld,%d) joins two member graphs", (long long)v, u);
+      // symmetric: v in row u with the same weight
+      const int32_t* b = col + rp[u];
+      const int32_t* e = col + rp[u + 1];
+      const int32_t* f = std::lower_bound(b, e, (int32_t)v);
+      if (f == e || *f != v) return fail(MQO_EGRAPH, "edge (%lld,%d) has no reverse entry", (long long)v, u);
+      if (w && w[rp[u] + (f - b)] != w[j]) return fail(MQO_EGRAPH, "weight of (%lld,%d) is not symmetric", (long long)v, u);
+    }
+  }
+  return MQO_OK;
+}
+
+mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, const int64_t* rp_in,
+                       const int32_t* col_in, const int8_t* w_in, int32_t is_dev, cudaStream_t stream,
+                       mqo_graph* out) {
+  if (!out || !rp_in || (nnz > 0 && !col_in)) return fail(MQO_EINVAL, "null pointer argument");
+  *out = nullptr;
+  std::vector<int64_t> rp_h;
+  std::vector<int32_t> col_h;
+  std::vector<int8_t> w_h;
+  const int64_t* rp = rp_in;
+  const int32_t* col = col_in;
+  const int8_t* w = w_in;
+  if (is_dev) {
+    if (n < 1 || n >= (1LL << 31)) return fail(MQO_EINVAL, "n out of range");
+    rp_h.resize((size_t)n + 1);
+    col_h.resize((size_t)std::max<int64_t>(nnz, 1));
+    CKG(cudaStreamSynchronize(stream));
+    CKG(cudaMemcpy(rp_h.data(), rp_in, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+    if (nnz) CKG(cudaMemcpy(col_h.data(), col_in, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+    rp = rp_h.data();
+    col = col_h.data();
+    if (w_in) {
+      w_h.resize((size_t)std::max<int64_t>(nnz, 1));
+      if (nnz) CKG(cudaMemcpy(w_h.data(), w_in, nnz, cudaMemcpyDeviceToHost));
+      w = w_h.data();
+    }
+  }
+  std::vector<int64_t> offs_own;
+  if (!offs) {
+    offs_own = {0, n};
+    offs = offs_own.data();
+    G = 1;
+  } else {
+    if (G < 1) return fail(MQO_EINVAL, "num_graphs must be >= 1");
+    if (offs[0] != 0) return fail(MQO_EGRAPH, "node_offsets[0] must be 0");
+    for (int32_t g = 0; g < G; ++g)
+      if (offs[g + 1] <= offs[g]) return fail(MQO_EGRAPH, "member graph %d is empty", g);
+    n = offs[G];
+  }
+  mqo_status st = validate(n, nnz, rp, col, w, G > 1 ? offs : nullptr, G);
+  if (st != MQO_OK) return st;
+
+  auto* g = new mqo_graph_s();
+  g->n = n;
+  g->nnz = nnz;
+  g->G = G;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+  g->h_rp.resize((size_t)n + 1);
+  for (int64_t v = 0; v <= n; ++v) g->h_rp[(size_t)v] = (int32_t)rp[v];
+  std::vector<int32_t> off32((size_t)G + 1), dmax((size_t)G, 0);
+  std::vector<Item> items;
+  for (int32_t k = 0; k <= G; ++k) off32[(size_t)k] = (int32_t)offs[k];
+  for (int32_t k = 0; k < G; ++k) {
+    for (int64_t v = offs[k]; v < offs[k + 1]; ++v)
+      dmax[(size_t)k] = std::max<int32_t>(dmax[(size_t)k], (int32_t)(rp[v + 1] - rp[v]));
+    for (int64_t v0 = offs[k]; v0 < offs[k + 1]; v0 += kChunkNodes) {
+      Item it;
+      it.g = k;
+      it.v0 = (int32_t)v0;
+      it.v1 = (int32_t)std::min<int64_t>(v0 + kChunkNodes, offs[k + 1]);
+      it.pad = 0;
+      items.push_back(it);
+    }
+  }
+  g->num_items = (int32_t)items.size();
+  auto cleanup = [&](mqo_status s) {
+    mqo_graph_destroy(g);
+    return s;
+  };
+  if ((st = dalloc(&g->d_rp, (size_t)n + 1, nullptr)) != MQO_OK) return cleanup(st);
+  if ((st = dalloc(&g->d_col, (size_t)nnz, nullptr)) != MQO_OK) return cleanup(st);
+  if (w && (st = dalloc(&g->d_w, (size_t)nnz, nullptr)) != MQO_OK) return cleanup(st);
+  if ((st = dalloc(&g->d_off, (size_t)G + 1, nullptr)) != MQO_OK) return cleanup(st);
+  if ((st = dalloc(&g->d_dmax, (size_t)G, nullptr)) != MQO_OK) return cleanup(st);
+  if ((st = dalloc(&g->d_items, items.size(), nullptr)) != MQO_OK) return cleanup(st);
+  cudaError_t e = cudaSuccess;
+  e = cudaMemcpy(g->d_rp, g->h_rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz) e = cudaMemcpy(g->d_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && w && nnz) e = cudaMemcpy(g->d_w, w, nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_off, off32.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_dmax, dmax.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cleanup(fail(MQO_ECUDA, "graph upload: %s", cudaGetErrorString(e)));
+  *out = g;
+  return MQO_OK;
+}
+
+mqo_status build_heavy_plan(mqo_graph g) {
+  if (g->hp_built) return MQO_OK;
+  std::vector<int32_t> light, hrow, hj0, hj1, hrows, hfirst;
+  for (int64_t v = 0; v < g->n; ++v) {
+    const int32_t a = g->h_rp[(size_t)v], b = g->h_rp[(size_t)v + 1];
+    if (b - a <= kSplit) {
+      light.push_back((int32_t)v);
+    } else {
+      hrows.push_back((int32_t)v);
+      hfirst.push_back((int32_t)hrow.size());
+      for (int32_t j = a; j < b; j += kSplit) {
+        hrow.push_back((int32_t)v);
+        hj0.push_back(j);
+        hj1.push_back(std::min(j + kSplit, b));
+      }
+    }
+  }
+  hfirst.push_back((int32_t)hrow.size());
+  const size_t total = light.size() + 3 * hrow.size() + hrows.size() + hfirst.size();
+  mqo_status st = dalloc(&g->d_hp, total, nullptr);
+  if (st != MQO_OK) return st;
+  int32_t* p = g->d_hp;
+  auto put = [&](const std::vector<int32_t>& v) -> int32_t* {
+    int32_t* q = p;
+    if (!v.empty()) cudaMemcpy(q, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    p += v.size();
+    return q;
+  };
+  g->hp.light_rows = put(light);
+  g->hp.num_light = (int32_t)light.size();
+  g->hp.heavy_row = put(hrow);
+  g->hp.heavy_j0 = put(hj0);
+  g->hp.heavy_j1 = put(hj1);
+  g->hp.num_chunks = (int32_t)hrow.size();
+  g->hp.heavy_rows = put(hrows);
+  g->hp.heavy_first = put(hfirst);
+  g->hp.num_heavy = (int32_t)hrows.size();
+  CKG(cudaGetLastError());
+  g->hp_built = true;
+  return MQO_OK;
+}
+
+struct Scope {
+  mqo_solver s;
+  explicit Scope(mqo_solver s_) : s(s_) {
+    cudaEventRecord(s->ev_in, s->user);
+    cudaStreamWaitEvent(s->work, s->ev_in, 0);
+  }
+  ~Scope() {
+    cudaEventRecord(s->ev_out, s->work);
+    cudaStreamWaitEvent(s->user, s->ev_out, 0);
+  }
+};
+
+mqo_status poison(mqo_solver s, cudaError_t e, const char* what) {
+  s->poisoned = true;
+  return fail(MQO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CKS(call)                                 \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return poison(s, e_, #call); \
+  } while (0)
+
+#define CHECK_SOLVER(s)                                                             \
+  do {                                                                              \
+    if (!(s)) return fail(MQO_EINVAL, "null solver");                               \
+    if ((s)->poisoned) return fail(MQO_ESTATE, "solver poisoned by an earlier error"); \
+  } while (0)
+
+cudaError_t enqueue_tick(mqo_solver s) {
+  cudaError_t e;
+  const SolverDev& S = s->S;
+  const int G = S.g.num_graphs;
+  if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
+  if ((e = launch_apply(S, s->grid, s->work)) != cudaSuccess) return e;
+  if ((e = launch_step(S, S.ZXP, S.cnt, S.st, S.gflag + 2 * G, s->grid, s->work)) != cudaSuccess) return e;
+  for (int pass = 0; pass < 3; ++pass)
+    if ((e = launch_disc(S, pass, s->grid, s->work)) != cudaSuccess) return e;
+  return launch_tick_end(S, s->work);
+}
+
+cudaError_t enqueue_ls_tick(mqo_solver s, int mode) {
+  cudaError_t e;
+  const SolverDev& S = s->S;
+  if ((e = launch_ctrl(S, mode, nullptr, s->work)) != cudaSuccess) return e;
+  if ((e = launch_apply(S, s->grid, s->work)) != cudaSuccess) return e;
+  for (int pass = 0; pass < 3; ++pass)
+    if ((e = launch_disc(S, pass, s->grid, s->work)) != cudaSuccess) return e;
+  return launch_tick_end(S, s->work);
+}
+
+cudaError_t capture(mqo_solver s, int ticks, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t ek = cudaSuccess;
+  for (int i = 0; i < ticks && ek == cudaSuccess; ++i) ek = enqueue_tick(s);
+  e = cudaStreamEndCapture(s->work, &graph);
+  if (ek != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return ek;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mqo_last_error(void) { return g_err.c_str(); }
+
+const char* mqo_version(void) { return "mqo-gb300 0.1 (sm_103a)"; }
+
+mqo_status mqo_graph_create_csr(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                const int8_t* weights, int32_t is_device_ptr, void* cuda_stream, mqo_graph* out) {
+  return build_graph(1, nullptr, n, nnz, row_ptr, col_idx, weights, is_device_ptr, (cudaStream_t)cuda_stream, out);
+}
+
+mqo_status mqo_graph_create_packed(int32_t num_graphs, const int64_t* node_offsets, int64_t nnz,
+                                   const int64_t* row_ptr, const int32_t* col_idx, const int8_t* weights,
+                                   int32_t is_device_ptr, void* cuda_stream, mqo_graph* out) {
+  if (!node_offsets) return fail(MQO_EINVAL, "null node_offsets");
+  if (num_graphs < 1) return fail(MQO_EINVAL, "num_graphs must be >= 1");
+  std::vector<int64_t> offs(node_offsets, node_offsets + num_graphs + 1);
+  return build_graph(num_graphs, offs.data(), offs.back(), nnz, row_ptr, col_idx, weights, is_device_ptr,
+                     (cudaStream_t)cuda_stream, out);
+}
+
+mqo_status mqo_graph_destroy(mqo_graph g) {
+  if (!g) return MQO_OK;
+  cudaFree(g->d_rp);
+  cudaFree(g->d_col);
+  cudaFree(g->d_w);
+  cudaFree(g->d_off);
+  cudaFree(g->d_dmax);
+  cudaFree(g->d_items);
+  cudaFree(g->d_hp);
+  cudaFree(g->d_scratch);
+  delete g;
+  return MQO_OK;
+}
+
+mqo_status mqo_graph_info(mqo_graph g, int64_t* n, int64_t* nnz, int32_t* num_graphs) {
+  if (!g) return fail(MQO_EINVAL, "null graph");
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (num_graphs) *num_graphs = g->G;
+  return MQO_OK;
+}
+
+mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream, mqo_solver* out) {
+  if (!g || !p || !out) return fail(MQO_EINVAL, "null argument");
+  *out = nullptr;
+  const int B = p->batch;
+  if (B < 1 || B > 128 || (B & (B - 1))) return fail(MQO_EINVAL, "batch=%d must be a power of two in [1,128]", B);
+  if (p->problem != MQO_MIS && p->problem != MQO_MAXCUT) return fail(MQO_EINVAL, "unknown problem %d", p->problem);
+  if (p->problem == MQO_MIS && g->d_w) return fail(MQO_EINVAL, "MIS needs an unweighted graph");
+  if (p->problem == MQO_MIS && !(p->gamma > 1.0f)) return fail(MQO_EINVAL, "gamma must be > 1");
+  if (p->problem == MQO_MAXCUT && !(p->lambda_ > 0.0f && p->lambda_ < 2.0f))
+    return fail(MQO_EINVAL, "lambda must lie in (0,2)");
+  if (p->x_dtype < 0 || p->x_dtype > 2) return fail(MQO_EINVAL, "bad x_dtype");
+  if (!(p->v_dtype == MQO_F32 || p->v_dtype == p->x_dtype)) return fail(MQO_EINVAL, "v_dtype must be F32 or x_dtype");
+  if (p->descent_cap < 1) return fail(MQO_EINVAL, "descent_cap must be >= 1");
+  if (p->t_gs < 0) return fail(MQO_EINVAL, "t_gs must be >= 0");
+  if (!(p->rho >= 0.0 && p->rho < 1.0)) return fail(MQO_EINVAL, "rho must lie in [0,1)");
+  if (p->init_kind != 0 && p->init_kind != 1) return fail(MQO_EINVAL, "init_kind must be 0 or 1");
+
+  auto* s = new mqo_solver_s();
+  s->g = g;
+  s->p = *p;
+  s->user = (cudaStream_t)cuda_stream;
+  auto bail = [&](mqo_status st) {
+    mqo_solver_destroy(s);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(MQO_ECUDA, "stream/event creation failed"));
+  SolverDev& S = s->S;
+  S.g = g->dev();
+  S.p.problem = p->problem;
+  S.p.B = B;
+  S.p.x_dtype = p->x_dtype;
+  S.p.v_dtype = p->v_dtype;
+  S.p.alpha = p->alpha;
+  S.p.momentum = p->momentum;
+  S.p.gamma = p->gamma;
+  S.p.lambda_ = p->lambda_;
+  S.p.rho = p->rho;
+  S.p.sigma = p->sigma;
+  S.p.t_gs = p->t_gs;
+  S.p.cap = p->descent_cap;
+  S.p.init_kind = p->init_kind;
+  S.p.local_search = p->local_search;
+  S.p.repair = p->repair;
+  S.p.seed = p->seed;
+  S.B = B;
+  S.Bw = (B + 31) / 32;
+  const int64_t n = g->n, T = (int64_t)g->G * B;
+  s->pairs = (size_t)n * B;
+  s->words = (size_t)n * S.Bw;
+  s->x_bytes = s->pairs * dtype_size(p->x_dtype);
+  s->v_bytes = s->pairs * dtype_size(p->v_dtype);
+  mqo_status st;
+  char *x0, *x1, *vv;
+  if ((st = dalloc(&x0, s->x_bytes, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&x1, s->x_bytes, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&vv, s->v_bytes, &s->allocs)) != MQO_OK) return bail(st);
+  S.X0 = x0;
+  S.X1 = x1;
+  S.V = vv;
+  uint32_t** wbufs[] = {&S.ZXP, &S.Zbest, &S.Zwork, &S.Zaux, &S.Zfree, &S.Zdrop, &s->d_zplain};
+  for (auto pp : wbufs)
+    if ((st = dalloc(pp, s->words, &s->allocs)) != MQO_OK) return bail(st);
+  int32_t** ibufs[] = {&S.owner, &S.pa, &S.pb, &S.gain};
+  for (auto pp : ibufs)
+    if ((st = dalloc(pp, s->pairs, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.st, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.cnt, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&s->d_cnt_plain, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&s->d_eval, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.tick, 1, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.gflag, (size_t)3 * g->G, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.any, 4, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&s->d_pending, 1, &s->allocs)) != MQO_OK) return bail(st);
+  if (cudaMallocHost(&s->h_pending, sizeof(int32_t)) != cudaSuccess) return bail(fail(MQO_ENOMEM, "pinned alloc"));
+  s->grid = std::max(1, std::min(g->num_items, g->sms * 8));
+  {
+    cudaEventRecord(s->ev_in, s->user);
+    cudaStreamWaitEvent(s->work, s->ev_in, 0);
+    cudaMemsetAsync(S.tick, 0, sizeof(int64_t), s->work);
+    cudaMemsetAsync(S.gflag, 0, sizeof(int32_t) * 3 * g->G, s->work);
+    cudaMemsetAsync(S.any, 0, sizeof(int32_t) * 4, s->work);
+    cudaMemsetAsync(x1, 0, s->x_bytes, s->work);
+    cudaEventRecord(s->ev_out, s->work);
+    cudaStreamWaitEvent(s->user, s->ev_out, 0);
+  }
+  if (cudaGetLastError() != cudaSuccess) return bail(fail(MQO_ECUDA, "solver setup failed"));
+  *out = s;
+  return mqo_init(s);
+}
+
+mqo_status mqo_solver_destroy(mqo_solver s) {
+  if (!s) return MQO_OK;
+  if (s->work) cudaStreamSynchronize(s->work);
+  if (s->gx1) cudaGraphExecDestroy(s->gx1);
+  if (s->gx16) cudaGraphExecDestroy(s->gx16);
+  for (void* q : s->allocs) cudaFree(q);
+  cudaFree(s->d_save);
+  if (s->h_pending) cudaFreeHost(s->h_pending);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_out) cudaEventDestroy(s->ev_out);
+  if (s->work) cudaStreamDestroy(s->work);
+  delete s;
+  return MQO_OK;
+}
+
+mqo_status mqo_init(mqo_solver s) {
+  CHECK_SOLVER(s);
+  Scope sc(s);
+  SolverDev& S = s->S;
+  CKS(cudaMemsetAsync(S.V, 0, s->v_bytes, s->work));
+  for (uint32_t* w : {S.ZXP, S.Zbest, S.Zwork, S.Zaux, S.Zfree, S.Zdrop, s->d_zplain})
+    CKS(cudaMemsetAsync(w, 0, s->words * sizeof(uint32_t), s->work));
+  CKS(cudaMemsetAsync(S.owner, 0x7f, s->pairs * sizeof(int32_t), s->work));
+  CKS(cudaMemsetAsync(S.pa, 0xff, s->pairs * sizeof(int32_t), s->work));
+  CKS(cudaMemsetAsync(S.pb, 0xff, s->pairs * sizeof(int32_t), s->work));
+  CKS(cudaMemsetAsync(S.gain, 0, s->pairs * sizeof(int32_t), s->work));
+  CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B, s->work));
+  CKS(launch_state_init(S, s->work));
+  CKS(launch_apply(S, s->grid, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_run(mqo_solver s, int64_t nticks) {
+  CHECK_SOLVER(s);
+  if (nticks < 0) return fail(MQO_EINVAL, "nticks < 0");
+  Scope sc(s);
+  if (!s->gx1) {
+    CKS(capture(s, 1, &s->gx1));
+    CKS(capture(s, 16, &s->gx16));
+  }
+  int64_t left = nticks;
+  while (left >= 16) {
+    CKS(cudaGraphLaunch(s->gx16, s->work));
+    left -= 16;
+  }
+  while (left-- > 0) CKS(cudaGraphLaunch(s->gx1, s->work));
+  s->host_tick += nticks;
+  return MQO_OK;
+}
+
+mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* step_ms, int64_t* launches) {
+  CHECK_SOLVER(s);
+  if (nticks < 0) return fail(MQO_EINVAL, "nticks < 0");
+  std::vector<cudaEvent_t> ev((size_t)2 * nticks);
+  for (auto& e : ev) CKS(cudaEventCreate(&e));
+  cudaError_t err = cudaSuccess;
+  {
+    Scope sc(s);
+    const SolverDev& S = s->S;
+    const int G = S.g.num_graphs;
+    for (int64_t k = 0; k < nticks && err == cudaSuccess; ++k) {
+      err = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
+      if (err == cudaSuccess) err = launch_apply(S, s->grid, s->work);
+      if (err == cudaSuccess) err = cudaEventRecord(ev[(size_t)2 * k], s->work);
+      if (err == cudaSuccess) err = launch_step(S, S.ZXP, S.cnt, S.st, S.gflag + 2 * G, s->grid, s->work);
+      if (err == cudaSuccess) err = cudaEventRecord(ev[(size_t)2 * k + 1], s->work);
+      for (int pass = 0; pass < 3 && err == cudaSuccess; ++pass) err = launch_disc(S, pass, s->grid, s->work);
+      if (err == cudaSuccess) err = launch_tick_end(S, s->work);
+    }
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s->work);
+  double total = 0.0;
+  for (int64_t k = 0; k < nticks && err == cudaSuccess; ++k) {
+    float ms = 0.0f;
+    err = cudaEventElapsedTime(&ms, ev[(size_t)2 * k], ev[(size_t)2 * k + 1]);
+    total += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return poison(s, err, "mqo_run_timed");
+  s->host_tick += nticks;
+  if (step_ms) *step_ms = total;
+  if (launches) *launches = nticks;
+  return MQO_OK;
+}
+
+mqo_status mqo_solve(mqo_solver s, int64_t nticks) {
+  mqo_status st = mqo_init(s);
+  if (st != MQO_OK) return st;
+  return mqo_run(s, nticks);
+}
+
+mqo_status mqo_step(mqo_solver s, int32_t nsteps) {
+  CHECK_SOLVER(s);
+  if (nsteps < 0) return fail(MQO_EINVAL, "nsteps < 0");
+  Scope sc(s);
+  const SolverDev& S = s->S;
+  for (int32_t i = 0; i < nsteps; ++i) {
+    CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B, s->work));
+    CKS(launch_step(S, s->d_zplain, s->d_cnt_plain, nullptr, nullptr, s->grid, s->work));
+    CKS(launch_tick_end(S, s->work));
+  }
+  s->host_tick += nsteps;
+  return MQO_OK;
+}
+
+mqo_status mqo_step_stats(mqo_solver s, int64_t* value, int64_t* a, int64_t* b) {
+  CHECK_SOLVER(s);
+  Scope sc(s);
+  CKS(launch_counters_out(s->S, s->d_cnt_plain, value, a, b, 0, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_reset(mqo_solver s, const uint8_t* traj_mask) {
+  CHECK_SOLVER(s);
+  Scope sc(s);
+  CKS(launch_ctrl(s->S, CTRL_RESET, traj_mask, s->work));
+  CKS(launch_apply(s->S, s->grid, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_round(mqo_solver s, uint32_t* z_bits) {
+  CHECK_SOLVER(s);
+  if (!z_bits) return fail(MQO_EINVAL, "null z_bits");
+  Scope sc(s);
+  CKS(launch_round_bits(s->S, z_bits, s->grid, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_evaluate(mqo_solver s, const uint32_t* z_bits, int64_t* value, int64_t* conflicts,
+                        int64_t* uncovered) {
+  CHECK_SOLVER(s);
+  if (!z_bits) return fail(MQO_EINVAL, "null z_bits");
+  Scope sc(s);
+  const SolverDev& S = s->S;
+  CKS(cudaMemsetAsync(s->d_eval, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B, s->work));
+  CKS(launch_eval(S, z_bits, s->d_eval, s->grid, s->work));
+  CKS(launch_counters_out(S, s->d_eval, value, conflicts, uncovered, 1, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds) {
+  CHECK_SOLVER(s);
+  if (max_rounds < 1) return fail(MQO_EINVAL, "max_rounds must be >= 1");
+  Scope sc(s);
+  SolverDev& S = s->S;
+  const size_t T = (size_t)S.g.num_graphs * S.B;
+  const size_t wb = s->words * sizeof(uint32_t), pbytes = s->pairs * sizeof(int32_t);
+  const size_t save_bytes = T * sizeof(TrajState) + T * sizeof(Counters) + 4 * wb + 4 * pbytes;
+  if (!s->d_save) CKS(cudaMalloc(&s->d_save, save_bytes));
+  char* q = static_cast<char*>(s->d_save);
+  TrajState* sv_st = reinterpret_cast<TrajState*>(q);
+  q += T * sizeof(TrajState);
+  struct Pair {
+    void* dst;
+    void* src;
+    size_t n;
+  };
+  std::vector<Pair> saves = {{q, S.cnt, T * sizeof(Counters)}};
+  q += T * sizeof(Counters);
+  for (uint32_t* w : {S.Zwork, S.Zaux, S.Zfree, S.Zdrop}) {
+    saves.push_back({q, w, wb});
+    q += wb;
+  }
+  for (int32_t* w : {S.owner, S.pa, S.pb, S.gain}) {
+    saves.push_back({q, w, pbytes});
+    q += pbytes;
+  }
+  CKS(cudaMemcpyAsync(sv_st, S.st, T * sizeof(TrajState), cudaMemcpyDeviceToDevice, s->work));
+  for (auto& pr : saves) CKS(cudaMemcpyAsync(pr.dst, pr.src, pr.n, cudaMemcpyDeviceToDevice, s->work));
+  int64_t ticks = 0;
+  CKS(enqueue_ls_tick(s, CTRL_LS_BEGIN));
+  ++ticks;
+  for (int32_t r = 0; r < max_rounds; ++r) {
+    CKS(enqueue_ls_tick(s, CTRL_LS));
+    ++ticks;
+    CKS(launch_any_pending(S, s->d_pending, s->work));
+    CKS(cudaMemcpyAsync(s->h_pending, s->d_pending, sizeof(int32_t), cudaMemcpyDeviceToHost, s->work));
+    CKS(cudaStreamSynchronize(s->work));
+    if (*s->h_pending == 0) break;
+  }
+  if (ticks & 1) {  // keep the parity of the x buffers
+    CKS(launch_tick_end(S, s->work));
+    ++ticks;
+  }
+  s->host_tick += ticks;
+  CKS(launch_ls_merge(S, sv_st, s->work));
+  for (auto& pr : saves) CKS(cudaMemcpyAsync(pr.src, pr.dst, pr.n, cudaMemcpyDeviceToDevice, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits) {
+  CHECK_SOLVER(s);
+  const SolverDev& S = s->S;
+  const size_t T = (size_t)S.g.num_graphs * S.B;
+  {
+    Scope sc(s);
+    if (z_bits) CKS(cudaMemcpyAsync(z_bits, S.Zbest, s->words * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s->work));
+  }
+  if (values) {
+    std::vector<TrajState> h(T);
+    CKS(cudaStreamSynchronize(s->work));
+    CKS(cudaMemcpy(h.data(), S.st, T * sizeof(TrajState), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < T; ++i) values[i] = h[i].best;
+  }
+  CKS(cudaStreamSynchronize(s->user));
+  return MQO_OK;
+}
+
+mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
+  CHECK_SOLVER(s);
+  if (!out) return fail(MQO_EINVAL, "null out");
+  const size_t T = (size_t)s->S.g.num_graphs * s->S.B;
+  std::vector<TrajState> h(T);
+  CKS(cudaStreamSynchronize(s->user));
+  CKS(cudaStreamSynchronize(s->work));
+  CKS(cudaMemcpy(h.data(), s->S.st, T * sizeof(TrajState), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < T; ++i) {
+    mqo_traj_info& o = out[i];
+    const TrajState& t = h[i];
+    o.phase = t.phase;
+    o.s = t.s;
+    o.r = t.r;
+    o.o = t.o;
+    o.best = t.best;
+    o.ticks = t.ticks;
+    o.last_round = t.last_round;
+    o.pad0 = 0;
+    o.last_commits = t.last_commits;
+    o.ev_value = t.ev_value;
+    o.ev_a = t.ev_a;
+    o.ev_b = t.ev_b;
+    o.accepts = t.accepts;
+    o.descents = t.descents;
+  }
+  return MQO_OK;
+}
+
+mqo_status mqo_get_x(mqo_solver s, void* x_out) {
+  CHECK_SOLVER(s);
+  if (!x_out) return fail(MQO_EINVAL, "null x_out");
+  Scope sc(s);
+  const void* src = (s->host_tick & 1) ? s->S.X1 : s->S.X0;
+  CKS(cudaMemcpyAsync(x_out, src, s->x_bytes, cudaMemcpyDeviceToDevice, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_set_x(mqo_solver s, const void* x_in) {
+  CHECK_SOLVER(s);
+  if (!x_in) return fail(MQO_EINVAL, "null x_in");
+  Scope sc(s);
+  void* dst = (s->host_tick & 1) ? s->S.X1 : s->S.X0;
+  CKS(cudaMemcpyAsync(dst, x_in, s->x_bytes, cudaMemcpyDeviceToDevice, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_get_v(mqo_solver s, void* v_out) {
+  CHECK_SOLVER(s);
+  if (!v_out) return fail(MQO_EINVAL, "null v_out");
+  Scope sc(s);
+  CKS(cudaMemcpyAsync(v_out, s->S.V, s->v_bytes, cudaMemcpyDeviceToDevice, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_objective_f64(mqo_solver s, double* out) {
+  CHECK_SOLVER(s);
+  if (!out) return fail(MQO_EINVAL, "null out");
+  Scope sc(s);
+  const size_t T = (size_t)s->S.g.num_graphs * s->S.B;
+  CKS(cudaMemsetAsync(out, 0, T * sizeof(double), s->work));
+  CKS(launch_objective(s->S, out, s->grid, s->work));
+  return MQO_OK;
+}
+
+mqo_status mqo_fb_forward(mqo_graph g, const float* X, int32_t B, float lambda_, double* obj, void* cuda_stream) {
+  if (!g || !X || !obj) return fail(MQO_EINVAL, "null argument");
+  if (B < 1 || B > 256 || (B & (B - 1))) return fail(MQO_EINVAL, "B=%d must be a power of two in [1,256]", B);
+  mqo_status st = build_heavy_plan(g);
+  if (st != MQO_OK) return st;
+  const size_t need = (size_t)g->hp.num_chunks * B;
+  if (need > g->scratch_floats) {
+    cudaFree(g->d_scratch);
+    g->d_scratch = nullptr;
+    g->scratch_floats = 0;
+    if ((st = dalloc(&g->d_scratch, need, nullptr)) != MQO_OK) return st;
+    g->scratch_floats = need;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CKG(cudaMemsetAsync(obj, 0, sizeof(double) * B, s));
+  const int grid = g->sms * 8;
+  CKG(launch_fb(g->dev(), g->hp, X, B, lambda_, nullptr, nullptr, obj, g->d_scratch, grid, s));
+  return MQO_OK;
+}
+
+mqo_status mqo_spmm_grad(mqo_graph g, const float* X, const float* gout, float* G, int32_t B, float lambda_,
+                         void* cuda_stream) {
+  if (!g || !X || !G) return fail(MQO_EINVAL, "null argument");
+  if (B < 1 || B > 256 || (B & (B - 1))) return fail(MQO_EINVAL, "B=%d must be a power of two in [1,256]", B);
+  mqo_status st = build_heavy_plan(g);
+  if (st != MQO_OK) return st;
+  const size_t need = (size_t)g->hp.num_chunks * B;
+  if (need > g->scratch_floats) {
+    cudaFree(g->d_scratch);
+    g->d_scratch = nullptr;
+    g->scratch_floats = 0;
+    if ((st = dalloc(&g->d_scratch, need, nullptr)) != MQO_OK) return st;
+    g->scratch_floats = need;
+  }
+  const int grid = g->sms * 8;
+  CKG(launch_fb(g->dev(), g->hp, X, B, lambda_, gout, G, nullptr, g->d_scratch, grid, (cudaStream_t)cuda_stream));
+  return MQO_OK;
+}
+
+mqo_status mqo_pga_momentum_step(float* x, float* v, const float* grad, int64_t count, float lr, float mu, float lo,
+                                 float hi, void* cuda_stream) {
+  if (count < 0 || (count > 0 && (!x || !v || !grad))) return fail(MQO_EINVAL, "bad argument");
+  CKG(launch_momentum(x, v, grad, count, lr, mu, lo, hi, (cudaStream_t)cuda_stream));
+  return MQO_OK;
+}
+
+mqo_status mqo_pga_adam_step(float* x, float* m, float* u, const float* grad, int64_t count, float lr, float b1,
+                             float b2, float eps, int64_t t, float lo, float hi, void* cuda_stream) {
+  if (count < 0 || (count > 0 && (!x || !m || !u || !grad)) || t < 1) return fail(MQO_EINVAL, "bad argument");
+  CKG(launch_adam(x, m, u, grad, count, lr, b1, b2, eps, t, lo, hi, (cudaStream_t)cuda_stream));
+  return MQO_OK;
+}
+
+}  // extern "C"

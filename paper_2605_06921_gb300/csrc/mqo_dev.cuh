@@ -1,0 +1,298 @@
+// mqo_dev.cuh -- device-side types and helpers of the mQO CUDA library.
+//
+// Everything here is written for sm_103a and compiled with --fmad=false:
+// every float expression rounds once per operation, exactly as written, so
+// that the descent arithmetic is reproducible operation by operation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace mqo {
+
+enum : int { PROB_MIS = 0, PROB_MAXCUT = 1 };
+enum : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
+enum : int { PH_DESCENT = 0, PH_REPAIR = 1, PH_LS = 2, PH_IDLE = 3 };
+enum : int {
+  RD_NONE = -1,
+  RD_COUNT = 0,
+  RD_DROP = 1,
+  RD_COMPLETE = 2,
+  RD_SWAP = 3,
+  RD_FLIP1 = 4,
+  RD_FLIP2 = 5
+};
+// per-trajectory actions decided by the control kernel for one tick
+enum : int {
+  ACT_STEP = 1,        // take a descent step this tick
+  ACT_ACC_ZX = 2,      // best <- z of the x evaluated by the last step
+  ACT_ACC_WORK = 4,    // best <- work set (repaired / locally searched)
+  ACT_RESET = 8,       // x <- best set with R zeroed, V <- 0 (Alg. 1 steps 6-8)
+  ACT_INIT = 16,       // x <- fresh initialisation, V <- 0 (Alg. 1 step 2)
+  ACT_WORK_ZX = 32,    // work set <- z of the last step (repair entry)
+  ACT_WORK_BEST = 64,  // work set <- best set (local-search entry)
+  ACT_APPLY_MASK = ACT_ACC_ZX | ACT_ACC_WORK | ACT_RESET | ACT_INIT | ACT_WORK_ZX | ACT_WORK_BEST
+};
+
+struct Params {
+  int32_t problem, B, x_dtype, v_dtype;
+  float alpha, momentum, gamma, lambda_;
+  double rho;
+  float sigma;
+  int32_t t_gs, cap, init_kind, local_search, repair;
+  uint64_t seed;
+};
+
+// One trajectory of the tick machine (field meanings as mqo_traj_info).
+struct __align__(16) TrajState {
+  int32_t phase, s, r, o;
+  int64_t best, ticks;
+  int32_t last_round, round;  // round: discrete round of the current tick
+  int64_t last_commits;
+  int64_t ev_value, ev_a, ev_b;
+  int64_t accepts, descents;
+  int32_t act, ls_done;
+  uint32_t rkeys[6];
+  int64_t rk;
+};
+
+// Per-trajectory integer sums produced by one tick (value of MaxCut is 2*cut).
+struct Counters {
+  unsigned long long value, a, b, commits;
+};
+
+// A contiguous node range inside one member graph.
+struct Item {
+  int32_t g, v0, v1, pad;
+};
+
+struct GraphDev {
+  int32_t n, num_graphs;
+  int64_t nnz;
+  const int32_t* row_ptr;   // n+1
+  const int32_t* col;       // nnz, global ids
+  const int8_t* w;          // nnz or nullptr
+  const int32_t* node_off;  // num_graphs+1
+  const int32_t* dmax;      // num_graphs
+  const Item* items;
+  int32_t num_items;
+};
+
+struct SolverDev {
+  GraphDev g;
+  Params p;
+  int32_t B, Bw;
+  void* X0;
+  void* X1;
+  void* V;
+  uint32_t* ZXP;    // z of the x evaluated by the last descent step
+  uint32_t* Zbest;  // best set
+  uint32_t* Zwork;  // work set of repair / local search
+  uint32_t* Zaux;   // tight (MIS) / positive-gain (MaxCut) bits
+  uint32_t* Zfree;  // free (uncovered) bits
+  uint32_t* Zdrop;  // drop decisions of a repair round
+  int32_t* owner;   // [n*B] move ownership marks
+  int32_t* pa;      // [n*B] proposal endpoint a
+  int32_t* pb;      // [n*B] proposal endpoint b
+  int32_t* gain;    // [n*B] 1-flip gains (MaxCut)
+  TrajState* st;    // [G*B]
+  Counters* cnt;    // [G*B]
+  int64_t* tick;    // current tick number
+  int32_t* gflag;   // [3*G] tick stamps: any apply / any discrete / any step
+  int32_t* any;     // [4] per-tick "any trajectory" stamps (apply, disc, step)
+};
+
+// --------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11), device version.
+// --------------------------------------------------------------------------
+struct U64x4 {
+  uint64_t v[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                               uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint64_t h0 = __umul64hi(M0, c0), l0 = M0 * c0;
+    const uint64_t h1 = __umul64hi(M1, c2), l1 = M1 * c2;
+    const uint64_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = l1;
+    c2 = n2;
+    c3 = l0;
+    k0 += 0x9E3779B97F4A7C15ULL;
+    k1 += 0xBB67AE8584CAA73BULL;
+  }
+  U64x4 r;
+  r.v[0] = c0;
+  r.v[1] = c1;
+  r.v[2] = c2;
+  r.v[3] = c3;
+  return r;
+}
+
+constexpr uint64_t TAG_INIT = 1ULL;
+constexpr uint64_t TAG_RESET = 2ULL;
+
+__device__ __forceinline__ float unit24(uint64_t w) { return (float)(w >> 40) * (1.0f / 16777216.0f); }
+
+// --------------------------------------------------------------------------
+// Keyed permutation of {0..n-1}: Feistel network on ceil(log2 n) bits with
+// alternating half widths, lowbias32 round function, cycle walking.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t feistel_once(uint32_t v, int d, const uint32_t* k) {
+  int wl = d >> 1, wr = d - wl;
+  uint32_t L = v >> wr, R = v & ((1u << wr) - 1u);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const uint32_t f = mix32(R ^ k[i]) & ((1u << wl) - 1u);
+    const uint32_t nl = R, nr = L ^ f;
+    const int t = wl;
+    wl = wr;
+    wr = t;
+    L = nl;
+    R = nr;
+  }
+  return (L << wr) | R;
+}
+
+// sigma(v) for 0 <= v < n; the walk ends within 2^d steps (d <= 31).
+__device__ __forceinline__ uint32_t feistel_sigma(uint32_t n, const uint32_t* k, uint32_t v) {
+  if (n <= 1u) return v;
+  int d = 32 - __clz(n - 1u);
+  if (d < 2) d = 2;
+  uint32_t y = feistel_once(v, d, k);
+  for (uint32_t it = 0; y >= n && it < (1u << d); ++it) y = feistel_once(y, d, k);
+  return y;
+}
+
+// --------------------------------------------------------------------------
+// Storage types
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float to_f(T v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+template <typename T>
+__device__ __forceinline__ T from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+
+// VEC consecutive elements of T loaded / stored as one aligned access.
+template <typename T, int VEC>
+struct alignas(sizeof(T) * VEC) Pack {
+  T e[VEC];
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ Pack<T, VEC> ld_pack(const T* p) {
+  return *reinterpret_cast<const Pack<T, VEC>*>(p);
+}
+template <typename T, int VEC>
+__device__ __forceinline__ Pack<T, VEC> ld_pack_stream(const T* p) {
+  Pack<T, VEC> r;
+  if constexpr (sizeof(Pack<T, VEC>) == 16) {
+    int4 t = __ldcs(reinterpret_cast<const int4*>(p));
+    r = *reinterpret_cast<Pack<T, VEC>*>(&t);
+  } else if constexpr (sizeof(Pack<T, VEC>) == 8) {
+    int2 t = __ldcs(reinterpret_cast<const int2*>(p));
+    r = *reinterpret_cast<Pack<T, VEC>*>(&t);
+  } else if constexpr (sizeof(Pack<T, VEC>) == 4) {
+    int t = __ldcs(reinterpret_cast<const int*>(p));
+    r = *reinterpret_cast<Pack<T, VEC>*>(&t);
+  } else {
+    r = *reinterpret_cast<const Pack<T, VEC>*>(p);
+  }
+  return r;
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void st_pack(T* p, const Pack<T, VEC>& v) {
+  *reinterpret_cast<Pack<T, VEC>*>(p) = v;
+}
+
+__device__ __forceinline__ float clamp_box(float v, float lo, float hi) {
+  if (v < lo) return lo;
+  if (v > hi) return hi;
+  return v;
+}
+
+// --------------------------------------------------------------------------
+// Bit words: node-major, Bw words per node, trajectory b -> bit b%32 of
+// word b/32.  In the (node, trajectory) thread mapping used by the pair
+// kernels (trajectory fastest, blockDim a multiple of max(32, B)), every
+// word of a node is owned by the lanes of one warp, so word updates are
+// aggregated with ballots and written by one lane.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ bool get_bit(const uint32_t* words, int64_t v, int Bw, int b) {
+  return (words[v * Bw + (b >> 5)] >> (b & 31)) & 1u;
+}
+
+// Update the calling lane's bit in word `words[v*Bw + b/32]` to `val` where
+// `active`; all 32 lanes must call this together.
+__device__ __forceinline__ void update_word(uint32_t* words, int64_t v, int Bw, int b, int B, bool val, bool active) {
+  const unsigned full = 0xffffffffu;
+  const unsigned mv = __ballot_sync(full, val && active);
+  const unsigned ma = __ballot_sync(full, active);
+  const int lane = threadIdx.x & 31;
+  const int G = B < 32 ? B : 32;
+  const int gbase = lane & ~(G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const unsigned gv = (mv >> gbase) & gmask, ga = (ma >> gbase) & gmask;
+  if (lane == gbase && ga) {
+    uint32_t* wp = words + v * Bw + (b >> 5);
+    *wp = (*wp & ~ga) | (gv & ga);
+  }
+}
+
+// As update_word, but safe against concurrent atomic writers of other bits
+// of the same word (used where cross-node commits run in the same pass).
+__device__ __forceinline__ void update_word_atomic(uint32_t* words, int64_t v, int Bw, int b, int B, bool val,
+                                                   bool active) {
+  const unsigned full = 0xffffffffu;
+  const unsigned mv = __ballot_sync(full, val && active);
+  const unsigned ma = __ballot_sync(full, active);
+  const int lane = threadIdx.x & 31;
+  const int G = B < 32 ? B : 32;
+  const int gbase = lane & ~(G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const unsigned gv = (mv >> gbase) & gmask, ga = (ma >> gbase) & gmask;
+  if (lane == gbase && ga) {
+    uint32_t* wp = words + v * Bw + (b >> 5);
+    if (ga & ~gv) atomicAnd(wp, ~(ga & ~gv));
+    if (gv) atomicOr(wp, gv);
+  }
+}
+
+__device__ __forceinline__ bool sorted_contains(const int32_t* col, int32_t lo, int32_t hi, int32_t key) {
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t c = col[mid];
+    if (c == key) return true;
+    if (c < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return false;
+}
+
+}  // namespace mqo

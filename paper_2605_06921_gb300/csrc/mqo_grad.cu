@@ -1,0 +1,259 @@
+// mqo_grad.cu -- f_B forward / backward on a float32 block, and the
+// projected momentum / Adam updates that drive it (autograd path).
+//
+// f_B(x) = -lambda 1^T x - x^T A x (Eq. adj_lin_two_props), per column b of
+// X (n x B, node-major); grad f_B = -lambda 1 - 2 A x (proof of Thm 3.6).
+//
+// Power-law graphs have rows of very different length.  Rows of degree up
+// to kSplit are accumulated whole by one row group (CSR order); longer rows
+// are cut into chunks of kSplit entries whose partial sums go to scratch,
+// and a second kernel adds a row's chunk partials in chunk order.  The
+// objective is accumulated per lane in float32 over a few rows, then in
+// double, then reduced per block and across blocks with double atomics.
+#include "mqo_dev.cuh"
+#include "mqo_host.h"
+
+namespace mqo {
+
+template <int VEC>
+struct FbOut {
+  __device__ __forceinline__ static void emit(int64_t row, const float* acc, const float* X, int B, int b0,
+                                              float lambda_, const float* gout, float* G, bool want_obj,
+                                              float* objf) {
+    if (G) {
+      float o[VEC];
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float tt = 2.0f * acc[e];
+        float gr = -lambda_ - tt;
+        if (gout) gr = gout[b0 + e] * gr;
+        o[e] = gr;
+      }
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) G[row * B + b0 + e] = o[e];
+    }
+    if (want_obj) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float x = X[row * B + b0 + e];
+        const float t1 = lambda_ * x;
+        const float t2 = x * acc[e];
+        objf[e] = objf[e] - t1;
+        objf[e] = objf[e] - t2;
+      }
+    }
+  }
+};
+
+struct FbArgs {
+  GraphDev g;
+  HeavyPlan hp;
+  const float* X;
+  int B;
+  float lambda_;
+  const float* gout;
+  float* G;
+  double* obj;
+  float* scratch;
+};
+
+template <int VEC>
+__device__ __forceinline__ void flush_obj(float* objf, double* objd, int& pending) {
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    objd[e] += (double)objf[e];
+    objf[e] = 0.0f;
+  }
+  pending = 0;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) k_fb_units(FbArgs a) {
+  __shared__ double s_obj[256];
+  const int B = a.B;
+  const int lpr = B / VEC;
+  const int rpw = 32 / lpr;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / lpr;
+  const int l = lane - sub * lpr;
+  const int b0 = l * VEC;
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 * rpw + sub;
+  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / 32 * rpw;
+  const int64_t nunits = (int64_t)a.hp.num_light + a.hp.num_chunks;
+  const bool want_obj = a.obj != nullptr;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_obj[i] = 0.0;
+  __syncthreads();
+  float objf[VEC];
+  double objd[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) { objf[e] = 0.0f; objd[e] = 0.0; }
+  int pending = 0;
+  for (int64_t u = group; u < nunits; u += ngroups) {
+    int64_t row;
+    int32_t j0, j1;
+    const bool whole = u < a.hp.num_light;
+    if (whole) {
+      row = a.hp.light_rows[u];
+      j0 = a.g.row_ptr[row];
+      j1 = a.g.row_ptr[row + 1];
+    } else {
+      const int64_t c = u - a.hp.num_light;
+      row = a.hp.heavy_row[c];
+      j0 = a.hp.heavy_j0[c];
+      j1 = a.hp.heavy_j1[c];
+    }
+    float acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+    int j = j0;
+    for (; j + 4 <= j1; j += 4) {
+      const int c0 = __ldcs(a.g.col + j), c1 = __ldcs(a.g.col + j + 1), c2 = __ldcs(a.g.col + j + 2),
+                c3 = __ldcs(a.g.col + j + 3);
+      const Pack<float, VEC> p0 = ld_pack<float, VEC>(a.X + (int64_t)c0 * B + b0);
+      const Pack<float, VEC> p1 = ld_pack<float, VEC>(a.X + (int64_t)c1 * B + b0);
+      const Pack<float, VEC> p2 = ld_pack<float, VEC>(a.X + (int64_t)c2 * B + b0);
+      const Pack<float, VEC> p3 = ld_pack<float, VEC>(a.X + (int64_t)c3 * B + b0);
+      const int8_t w0 = a.g.w ? a.g.w[j] : 1, w1 = a.g.w ? a.g.w[j + 1] : 1, w2 = a.g.w ? a.g.w[j + 2] : 1,
+                   w3 = a.g.w ? a.g.w[j + 3] : 1;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        acc[e] = w0 >= 0 ? acc[e] + p0.e[e] : acc[e] - p0.e[e];
+        acc[e] = w1 >= 0 ? acc[e] + p1.e[e] : acc[e] - p1.e[e];
+        acc[e] = w2 >= 0 ? acc[e] + p2.e[e] : acc[e] - p2.e[e];
+        acc[e] = w3 >= 0 ? acc[e] + p3.e[e] : acc[e] - p3.e[e];
+      }
+    }
+    for (; j < j1; ++j) {
+      const int c = __ldcs(a.g.col + j);
+      const int8_t w = a.g.w ? a.g.w[j] : 1;
+      const Pack<float, VEC> p = ld_pack<float, VEC>(a.X + (int64_t)c * B + b0);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = w >= 0 ? acc[e] + p.e[e] : acc[e] - p.e[e];
+    }
+    if (whole) {
+      FbOut<VEC>::emit(row, acc, a.X, B, b0, a.lambda_, a.gout, a.G, want_obj, objf);
+      if (++pending == 16) flush_obj<VEC>(objf, objd, pending);
+    } else {
+      const int64_t c = u - a.hp.num_light;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) a.scratch[c * B + b0 + e] = acc[e];
+    }
+  }
+  if (want_obj) {
+    flush_obj<VEC>(objf, objd, pending);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+      if (objd[e] != 0.0) atomicAdd(&s_obj[b0 + e], objd[e]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+      if (s_obj[i] != 0.0) atomicAdd(&a.obj[i], s_obj[i]);
+  }
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) k_fb_heavy(FbArgs a) {
+  __shared__ double s_obj[256];
+  const int B = a.B;
+  const int lpr = B / VEC;
+  const int rpw = 32 / lpr;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / lpr;
+  const int l = lane - sub * lpr;
+  const int b0 = l * VEC;
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 * rpw + sub;
+  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / 32 * rpw;
+  const bool want_obj = a.obj != nullptr;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_obj[i] = 0.0;
+  __syncthreads();
+  float objf[VEC];
+  double objd[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) { objf[e] = 0.0f; objd[e] = 0.0; }
+  int pending = 0;
+  for (int64_t h = group; h < a.hp.num_heavy; h += ngroups) {
+    const int64_t row = a.hp.heavy_rows[h];
+    const int32_t c0 = a.hp.heavy_first[h], c1 = a.hp.heavy_first[h + 1];
+    float acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+    for (int32_t c = c0; c < c1; ++c) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = acc[e] + a.scratch[(int64_t)c * B + b0 + e];
+    }
+    FbOut<VEC>::emit(row, acc, a.X, B, b0, a.lambda_, a.gout, a.G, want_obj, objf);
+    if (++pending == 16) flush_obj<VEC>(objf, objd, pending);
+  }
+  if (want_obj) {
+    flush_obj<VEC>(objf, objd, pending);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+      if (objd[e] != 0.0) atomicAdd(&s_obj[b0 + e], objd[e]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+      if (s_obj[i] != 0.0) atomicAdd(&a.obj[i], s_obj[i]);
+  }
+}
+
+template <int VEC>
+static cudaError_t launch_fb_vec(const FbArgs& a, int grid, cudaStream_t s) {
+  if ((int64_t)a.hp.num_light + a.hp.num_chunks > 0) k_fb_units<VEC><<<grid, 256, 0, s>>>(a);
+  if (a.hp.num_heavy > 0) k_fb_heavy<VEC><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fb(const GraphDev& g, const HeavyPlan& hp, const float* X, int B, float lambda_,
+                      const float* gout, float* G, double* obj, float* scratch, int grid, cudaStream_t stream) {
+  FbArgs a{g, hp, X, B, lambda_, gout, G, obj, scratch};
+  const int vec = B >= 32 ? B / 32 : 1;
+  switch (vec) {
+    case 1: return launch_fb_vec<1>(a, grid, stream);
+    case 2: return launch_fb_vec<2>(a, grid, stream);
+    case 4: return launch_fb_vec<4>(a, grid, stream);
+    case 8: return launch_fb_vec<8>(a, grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------- optimisers
+__global__ void k_momentum(float* x, float* v, const float* grad, int64_t n, float lr, float mu, float lo, float hi) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = mu * v[i];
+    const float vn = a + grad[i];
+    v[i] = vn;
+    const float step = lr * vn;
+    x[i] = clamp_box(x[i] + step, lo, hi);
+  }
+}
+
+__global__ void k_adam(float* x, float* m, float* u, const float* grad, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2, float lo, float hi) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = grad[i];
+    const float mn = b1 * m[i] + (1.0f - b1) * g;
+    const float un = b2 * u[i] + (1.0f - b2) * (g * g);
+    m[i] = mn;
+    u[i] = un;
+    const float mh = mn * c1;
+    const float uh = un * c2;
+    const float step = lr * mh / (sqrtf(uh) + eps);
+    x[i] = clamp_box(x[i] + step, lo, hi);
+  }
+}
+
+cudaError_t launch_momentum(float* x, float* v, const float* grad, int64_t n, float lr, float mu, float lo,
+                            float hi, cudaStream_t stream) {
+  const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+  if (n > 0) k_momentum<<<grid, 256, 0, stream>>>(x, v, grad, n, lr, mu, lo, hi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* x, float* m, float* u, const float* grad, int64_t n, float lr, float b1, float b2,
+                        float eps, int64_t t, float lo, float hi, cudaStream_t stream) {
+  const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+  const float c1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+  const float c2 = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+  if (n > 0) k_adam<<<grid, 256, 0, stream>>>(x, m, u, grad, n, lr, b1, b2, eps, c1, c2, lo, hi);
+  return cudaGetLastError();
+}
+
+}  // namespace mqo

@@ -1,0 +1,50 @@
+// mqo_host.h -- launchers shared by the host runtime of the mQO library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mqo_dev.cuh"
+
+namespace mqo {
+
+constexpr int kPairThreads = 256;  // pair kernels: (node, trajectory) per thread
+
+enum CtrlMode : int { CTRL_MACHINE = 0, CTRL_LS_BEGIN = 1, CTRL_LS = 2, CTRL_RESET = 3 };
+
+cudaError_t launch_step(const SolverDev& S, uint32_t* zout, Counters* cnt, const TrajState* st,
+                        const int32_t* gflag_step, int grid, cudaStream_t stream);
+
+cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream);
+cudaError_t launch_apply(const SolverDev& S, int grid, cudaStream_t stream);
+cudaError_t launch_disc(const SolverDev& S, int pass, int grid, cudaStream_t stream);
+cudaError_t launch_tick_end(const SolverDev& S, cudaStream_t stream);
+cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, int grid, cudaStream_t stream);
+cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, int grid, cudaStream_t stream);
+cudaError_t launch_counters_out(const SolverDev& S, const Counters* c, int64_t* value, int64_t* a, int64_t* b,
+                                int kind, cudaStream_t stream);
+cudaError_t launch_objective(const SolverDev& S, double* out, int grid, cudaStream_t stream);
+cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStream_t stream);
+cudaError_t launch_state_init(const SolverDev& S, cudaStream_t stream);
+cudaError_t launch_any_pending(const SolverDev& S, int32_t* out, cudaStream_t stream);
+
+// graph-level kernels (autograd path)
+struct HeavyPlan {
+  const int32_t* light_rows;  // rows handled whole
+  int32_t num_light;
+  const int32_t* heavy_row;   // per chunk: row
+  const int32_t* heavy_j0;    // per chunk: first entry
+  const int32_t* heavy_j1;    // per chunk: end entry
+  int32_t num_chunks;
+  const int32_t* heavy_rows;  // distinct heavy rows
+  const int32_t* heavy_first; // per heavy row: first chunk
+  int32_t num_heavy;
+};
+
+cudaError_t launch_fb(const GraphDev& g, const HeavyPlan& hp, const float* X, int B, float lambda_,
+                      const float* gout, float* G, double* obj, float* scratch, int grid, cudaStream_t stream);
+cudaError_t launch_momentum(float* x, float* v, const float* grad, int64_t n, float lr, float mu, float lo,
+                            float hi, cudaStream_t stream);
+cudaError_t launch_adam(float* x, float* m, float* u, const float* grad, int64_t n, float lr, float b1, float b2,
+                        float eps, int64_t t, float lo, float hi, cudaStream_t stream);
+
+}  // namespace mqo

@@ -1,0 +1,767 @@
+// mqo_tick.cu -- the per-trajectory machine of Alg. 1 / Alg. 2 on the GPU.
+//
+// One tick = control (one thread per trajectory) -> apply (accept copies,
+// resets, initialisations) -> fused descent step -> discrete round passes
+// A, B and the count pass C -> tick end.  The control kernel decides, from
+// the exact counters of the previous tick, what each trajectory does now;
+// the node-parallel kernels then act on (node, trajectory) pairs.  Member
+// graphs with nothing to do in a pass are skipped through per-graph tick
+// stamps written by the control kernel.
+#include "mqo_dev.cuh"
+#include "mqo_host.h"
+
+namespace mqo {
+
+// ---------------------------------------------------------------- control
+struct CtrlArgs {
+  SolverDev S;
+  int mode;
+  const uint8_t* mask;
+};
+
+__device__ __forceinline__ void reset_keys(const Params& p, int64_t tau, int32_t o, int32_t r, int32_t n_g,
+                                           TrajState& st) {
+  const U64x4 k = philox4x64_10(TAG_RESET, (uint64_t)o, (uint64_t)r, 0ULL, p.seed, (uint64_t)tau);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    st.rkeys[2 * i] = (uint32_t)(k.v[i] & 0xffffffffULL);
+    st.rkeys[2 * i + 1] = (uint32_t)(k.v[i] >> 32);
+  }
+  st.rk = (int64_t)floor(p.rho * (double)n_g);
+}
+
+__global__ void k_ctrl(CtrlArgs A) {
+  const SolverDev& S = A.S;
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  const int64_t tau = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tau >= T) return;
+  const int64_t t = *S.tick;
+  const int g = (int)(tau / S.B);
+  const int32_t n_g = S.g.node_off[g + 1] - S.g.node_off[g];
+  const Params& p = S.p;
+  const bool mis = p.problem == PROB_MIS;
+  TrajState st = S.st[tau];
+  Counters c = S.cnt[tau];
+  S.cnt[tau] = Counters{0ull, 0ull, 0ull, 0ull};
+  int act = 0;
+  int round = RD_NONE;
+
+  auto accept = [&](int bit, int64_t value) {
+    if (value > st.best) {
+      st.best = value;
+      act |= bit;
+      st.accepts += 1;
+    }
+  };
+
+  if (A.mode == CTRL_RESET) {
+    // forced reset (mqo_reset): round r+1 from the best set, new descent
+    if (A.mask == nullptr || A.mask[tau]) {
+      st.r += 1;
+      st.s = 0;
+      st.phase = PH_DESCENT;
+      reset_keys(p, tau, st.o, st.r, n_g, st);
+      act = ACT_RESET;
+    }
+    st.act = act;
+    st.round = RD_NONE;
+    S.st[tau] = st;
+    S.cnt[tau] = c;  // a forced reset leaves the last counters in place
+    if (act) {
+      S.gflag[g] = (int32_t)(t + 1);
+      S.any[0] = (int32_t)(t + 1);
+    }
+    return;
+  }
+
+  // fold the previous tick's exact counters
+  const int64_t cv = (int64_t)c.value;
+  st.ev_value = mis ? cv : cv / 2;
+  st.ev_a = (int64_t)c.a;
+  st.ev_b = (int64_t)c.b;
+  st.last_commits = (int64_t)c.commits;
+
+  if (A.mode == CTRL_LS_BEGIN) {
+    st.ls_done = 0;
+    act = ACT_WORK_BEST;
+    round = RD_COUNT;
+    st.last_round = RD_COUNT;
+  } else if (A.mode == CTRL_LS) {
+    if (!st.ls_done) {
+      bool done;
+      if (mis) {
+        if (st.ev_b > 0) { round = RD_COMPLETE; done = false; }
+        else if (!(st.last_round == RD_SWAP && st.last_commits == 0)) { round = RD_SWAP; done = false; }
+        else done = true;
+      } else {
+        if (st.ev_b > 0) { round = RD_FLIP1; done = false; }
+        else if (!(st.last_round == RD_FLIP2 && st.last_commits == 0)) { round = RD_FLIP2; done = false; }
+        else done = true;
+      }
+      if (done) {
+        accept(ACT_ACC_WORK, st.ev_value);
+        st.ls_done = 1;
+        round = RD_NONE;
+      }
+      st.last_round = round;
+    }
+  } else {
+    // ----- the machine (same decisions as the oracle's control step) -----
+    auto start_outer = [&]() {
+      st.o += 1;
+      st.r = 0;
+      st.s = 0;
+      st.phase = PH_DESCENT;
+      act |= ACT_INIT;
+    };
+    auto after_accept = [&]() -> int {
+      if (st.r < p.t_gs) {
+        st.r += 1;
+        st.s = 0;
+        st.phase = PH_DESCENT;
+        reset_keys(p, tau, st.o, st.r, n_g, st);
+        act |= ACT_RESET;
+        return RD_NONE;
+      }
+      if (p.local_search) {
+        st.phase = PH_LS;
+        act |= ACT_WORK_BEST;
+        return RD_COUNT;
+      }
+      start_outer();
+      return RD_NONE;
+    };
+    if (st.phase == PH_DESCENT) {
+      if (st.s > 0) {
+        const bool pass = mis ? (st.ev_a == 0 && st.ev_b == 0) : (st.ev_a == 0);
+        if (pass) {
+          st.descents += 1;
+          accept(ACT_ACC_ZX, st.ev_value);
+          round = after_accept();
+        } else if (st.s >= p.cap) {
+          st.descents += 1;
+          if (mis) {
+            if (p.repair) {
+              st.phase = PH_REPAIR;
+              act |= ACT_WORK_ZX;
+              round = RD_COUNT;
+            } else {
+              round = after_accept();
+            }
+          } else {
+            accept(ACT_ACC_ZX, st.ev_value);
+            round = after_accept();
+          }
+        }
+      }
+    } else if (st.phase == PH_REPAIR) {
+      if (st.ev_a > 0) round = RD_DROP;
+      else if (st.ev_b > 0) round = RD_COMPLETE;
+      else {
+        accept(ACT_ACC_WORK, st.ev_value);
+        round = after_accept();
+      }
+    } else if (st.phase == PH_LS) {
+      bool done;
+      if (mis) {
+        if (st.ev_b > 0) { round = RD_COMPLETE; done = false; }
+        else if (!(st.last_round == RD_SWAP && st.last_commits == 0)) { round = RD_SWAP; done = false; }
+        else done = true;
+      } else {
+        if (st.ev_b > 0) { round = RD_FLIP1; done = false; }
+        else if (!(st.last_round == RD_FLIP2 && st.last_commits == 0)) { round = RD_FLIP2; done = false; }
+        else done = true;
+      }
+      if (done) {
+        accept(ACT_ACC_WORK, st.ev_value);
+        start_outer();
+        round = RD_NONE;
+      }
+    }
+    if (st.phase == PH_DESCENT) {
+      act |= ACT_STEP;
+      st.s += 1;
+      st.last_round = RD_NONE;
+      round = RD_NONE;
+    } else {
+      st.last_round = round;
+    }
+    st.ticks += 1;
+  }
+  st.act = act;
+  st.round = round;
+  S.st[tau] = st;
+  const int32_t stamp = (int32_t)(t + 1);
+  const int G = S.g.num_graphs;
+  if (act & ACT_APPLY_MASK) {
+    S.gflag[g] = stamp;
+    S.any[0] = stamp;
+  }
+  if (round != RD_NONE) {
+    S.gflag[G + g] = stamp;
+    S.any[1] = stamp;
+  }
+  if (act & ACT_STEP) {
+    S.gflag[2 * G + g] = stamp;
+    S.any[2] = stamp;
+  }
+}
+
+cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream) {
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  CtrlArgs a{S, mode, mask};
+  k_ctrl<<<(unsigned)((T + 127) / 128), 128, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void k_tick_end(int64_t* tick) { *tick += 1; }
+
+cudaError_t launch_tick_end(const SolverDev& S, cudaStream_t stream) {
+  k_tick_end<<<1, 1, 0, stream>>>(S.tick);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- pair-kernel frame
+// Every pair kernel walks the items; within an item, warp w of the block
+// covers pair indices [v0*B + 32k, ...) so that each warp holds whole bit
+// words.  `body(v, b, tau, in_range)` is called by all 32 lanes together.
+template <typename Body>
+__device__ __forceinline__ void for_pairs(const SolverDev& S, const int32_t* gstamp, int64_t stamp, Body body) {
+  const int B = S.B;
+  const int lane = threadIdx.x & 31;
+  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
+    const Item item = S.g.items[it];
+    if (gstamp && gstamp[item.g] != (int32_t)stamp) continue;
+    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
+    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+      const int64_t idx = base + lane;
+      const bool in = idx < hi;
+      const int64_t v = in ? idx / B : (int64_t)item.v0;
+      const int b = (int)(idx % B);
+      body(item.g, v, b, (int64_t)item.g * B + b, in);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- apply
+__global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
+  const int64_t t = *S.tick;
+  if (S.any[0] != (int32_t)(t + 1)) return;
+  const int B = S.B, Bw = S.Bw;
+  const bool mis = S.p.problem == PROB_MIS;
+  void* Xc = (t & 1) ? S.X1 : S.X0;
+  for_pairs(S, S.gflag, t + 1, [&](int g, int64_t v, int b, int64_t tau, bool in) {
+    const int act = in ? S.st[tau].act : 0;
+    const bool acc_zx = act & ACT_ACC_ZX, acc_w = act & ACT_ACC_WORK;
+    bool zb = false;
+    if (in) zb = get_bit(S.Zbest, v, Bw, b);
+    bool src = false;
+    if (acc_zx) src = get_bit(S.ZXP, v, Bw, b);
+    if (acc_w) src = get_bit(S.Zwork, v, Bw, b);
+    const bool acc = acc_zx || acc_w;
+    if (acc) zb = src;
+    update_word(S.Zbest, v, Bw, b, B, src, acc);
+    bool wv = false;
+    if (act & ACT_WORK_ZX) wv = get_bit(S.ZXP, v, Bw, b);
+    if (act & ACT_WORK_BEST) wv = zb;
+    update_word(S.Zwork, v, Bw, b, B, wv, (act & (ACT_WORK_ZX | ACT_WORK_BEST)) != 0);
+    if (act & (ACT_RESET | ACT_INIT)) {
+      const int32_t off = S.g.node_off[g];
+      const uint32_t vl = (uint32_t)(v - off);
+      float x;
+      if (act & ACT_RESET) {
+        const TrajState& st = S.st[tau];
+        x = zb ? 1.0f : (mis ? 0.0f : -1.0f);
+        const uint32_t n_g = (uint32_t)(S.g.node_off[g + 1] - off);
+        uint32_t keys[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) keys[i] = st.rkeys[i];
+        if ((int64_t)feistel_sigma(n_g, keys, vl) < st.rk) x = 0.0f;
+      } else {
+        const Params& p = S.p;
+        const int32_t o = S.st[tau].o;
+        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)o, (uint64_t)vl, 0ULL, p.seed, (uint64_t)tau);
+        const float lo = mis ? 0.0f : -1.0f, hi = 1.0f;
+        if (p.init_kind == 0) {
+          const float u = unit24(r.v[0]);
+          x = lo + (hi - lo) * u;
+        } else {
+          const int32_t d = S.g.row_ptr[v + 1] - S.g.row_ptr[v];
+          const int32_t dm = S.g.dmax[g];
+          const float q = dm > 0 ? (float)d / (float)dm : 0.0f;
+          float base = 1.0f - q;
+          if (!mis) base = 2.0f * base - 1.0f;
+          float s = unit24(r.v[0]) + unit24(r.v[1]);
+          s = s + unit24(r.v[2]);
+          s = s + unit24(r.v[3]);
+          s = s - 2.0f;
+          float eps = s * 1.7320508075688772f;
+          eps = p.sigma * eps;
+          x = clamp_box(base + eps, lo, hi);
+        }
+      }
+      const int64_t e = v * B + b;
+      if (S.p.x_dtype == DT_F32) static_cast<float*>(Xc)[e] = x;
+      else if (S.p.x_dtype == DT_BF16) static_cast<__nv_bfloat16*>(Xc)[e] = __float2bfloat16_rn(x);
+      else static_cast<__half*>(Xc)[e] = __float2half_rn(x);
+      if (S.p.v_dtype == DT_F32) static_cast<float*>(S.V)[e] = 0.0f;
+      else if (S.p.v_dtype == DT_BF16) static_cast<__nv_bfloat16*>(S.V)[e] = __float2bfloat16_rn(0.0f);
+      else static_cast<__half*>(S.V)[e] = __float2half_rn(0.0f);
+    }
+  });
+}
+
+cudaError_t launch_apply(const SolverDev& S, int grid, cudaStream_t stream) {
+  k_apply<<<grid, kPairThreads, 0, stream>>>(S);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- discrete rounds
+// Block-level counter reduction for pair kernels: per item, per trajectory.
+struct CntAcc {
+  long long v0, v1, v2, v3;
+};
+
+__device__ __forceinline__ void flush_counters(const SolverDev& S, unsigned long long* s_cnt, int g, int B,
+                                               Counters* dst) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) {
+    const unsigned long long val = s_cnt[i];
+    if (val) {
+      Counters* c = dst + (int64_t)g * B + i / 4;
+      const int k = i & 3;
+      unsigned long long* p = k == 0 ? &c->value : k == 1 ? &c->a : k == 2 ? &c->b : &c->commits;
+      atomicAdd(p, val);
+    }
+    s_cnt[i] = 0ull;
+  }
+  __syncthreads();
+}
+
+// pass 0 = A (decide / propose), 1 = B (commit), 2 = C (count)
+__global__ void __launch_bounds__(kPairThreads) k_disc(SolverDev S, int pass) {
+  __shared__ unsigned long long s_cnt[4 * 128];
+  const int64_t t = *S.tick;
+  if (S.any[1] != (int32_t)(t + 1)) return;
+  const int B = S.B, Bw = S.Bw;
+  const bool mis = S.p.problem == PROB_MIS;
+  const int G = S.g.num_graphs;
+  const int32_t* rp = S.g.row_ptr;
+  const int32_t* col = S.g.col;
+  const int8_t* wts = S.g.w;
+  for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
+    const Item item = S.g.items[it];
+    if (S.gflag[G + item.g] != (int32_t)(t + 1)) continue;
+    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
+    long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+    int my_b = -1;
+    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+      const int64_t idx = base + lane;
+      const bool in = idx < hi;
+      const int64_t v = in ? idx / B : (int64_t)item.v0;
+      const int b = (int)(idx % B);
+      const int64_t tau = (int64_t)item.g * B + b;
+      const int round = in ? S.st[tau].round : RD_NONE;
+      my_b = b;
+      const int64_t e = v * B + b;
+      const int32_t rs = rp[v], re = rp[v + 1];
+      if (pass == 0) {
+        // ---------------- pass A
+        bool dropv = false;
+        if (round == RD_DROP && get_bit(S.Zwork, v, Bw, b)) {
+          for (int32_t j = rs; j < re; ++j) {
+            const int32_t u = col[j];
+            if (u < v && get_bit(S.Zwork, u, Bw, b)) { dropv = true; break; }
+          }
+        }
+        update_word(S.Zdrop, v, Bw, b, B, dropv, round == RD_DROP);
+        acc3 += dropv;
+        bool addv = false;
+        if (round == RD_COMPLETE && get_bit(S.Zfree, v, Bw, b)) {
+          addv = true;
+          for (int32_t j = rs; j < re; ++j) {
+            const int32_t u = col[j];
+            if (u < v && get_bit(S.Zfree, u, Bw, b)) { addv = false; break; }
+          }
+        }
+        bool flipv = false;
+        if (round == RD_FLIP1 && get_bit(S.Zaux, v, Bw, b)) {
+          flipv = true;
+          for (int32_t j = rs; j < re; ++j) {
+            const int32_t u = col[j];
+            if (u < v && get_bit(S.Zaux, u, Bw, b)) { flipv = false; break; }
+          }
+        }
+        const bool zv = get_bit(S.Zwork, v, Bw, b);
+        // complete sets bits, flip1 toggles: both are own-word updates
+        update_word(S.Zwork, v, Bw, b, B, addv ? true : !zv, addv || flipv);
+        acc3 += addv + flipv;
+        if (round == RD_SWAP) {
+          int32_t fa = -1, fb = -1;
+          if (zv) {
+            for (int32_t i = rs; i < re && fa < 0; ++i) {
+              const int32_t a = col[i];
+              if (!get_bit(S.Zaux, a, Bw, b)) continue;
+              for (int32_t j = i + 1; j < re; ++j) {
+                const int32_t c = col[j];
+                if (!get_bit(S.Zaux, c, Bw, b)) continue;
+                if (!sorted_contains(col, rp[a], rp[a + 1], c)) { fa = a; fb = c; break; }
+              }
+            }
+          }
+          S.pa[e] = fa;
+          S.pb[e] = fb;
+          if (fa >= 0) {
+            S.owner[(int64_t)fa * B + b] = (int32_t)v;
+            S.owner[(int64_t)fb * B + b] = (int32_t)v;
+          }
+        }
+        if (round == RD_FLIP2) {
+          int32_t fb = -1;
+          const int32_t ga = S.gain[e];
+          for (int32_t j = rs; j < re; ++j) {
+            const int32_t u = col[j];
+            if (u <= v) continue;
+            if (get_bit(S.Zwork, u, Bw, b) == zv) continue;
+            const int w = wts ? (int)wts[j] : 1;
+            if (ga + S.gain[(int64_t)u * B + b] + 2 * w > 0) { fb = u; break; }
+          }
+          S.pb[e] = fb;
+          if (fb >= 0) {
+            atomicMin(&S.owner[e], (int32_t)v);
+            atomicMin(&S.owner[(int64_t)fb * B + b], (int32_t)v);
+          }
+        }
+      } else if (pass == 1) {
+        // ---------------- pass B
+        const bool dv = round == RD_DROP && get_bit(S.Zdrop, v, Bw, b);
+        update_word_atomic(S.Zwork, v, Bw, b, B, false, dv);
+        if (round == RD_SWAP) {
+          const int32_t fa = S.pa[e];
+          if (fa >= 0) {
+            const int32_t fb = S.pb[e];
+            bool ok = true;
+            const int32_t ends[2] = {fa, fb};
+            for (int k = 0; k < 2 && ok; ++k) {
+              const int32_t x = ends[k];
+              for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+                const int32_t o = S.owner[(int64_t)col[j] * B + b];
+                if (o < (int32_t)v) { ok = false; break; }
+              }
+            }
+            if (ok) {
+              const uint32_t bit = 1u << (b & 31);
+              atomicAnd(&S.Zwork[v * Bw + (b >> 5)], ~bit);
+              atomicOr(&S.Zwork[(int64_t)fa * Bw + (b >> 5)], bit);
+              atomicOr(&S.Zwork[(int64_t)fb * Bw + (b >> 5)], bit);
+              acc3 += 1;
+            }
+          }
+        }
+        if (round == RD_FLIP2) {
+          const int32_t fb = S.pb[e];
+          if (fb >= 0) {
+            bool ok = S.owner[e] == (int32_t)v && S.owner[(int64_t)fb * B + b] == (int32_t)v;
+            const int32_t ends[2] = {(int32_t)v, fb};
+            for (int k = 0; k < 2 && ok; ++k) {
+              const int32_t x = ends[k];
+              for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+                const int32_t y = col[j];
+                if (y == (int32_t)v || y == fb) continue;
+                if (S.owner[(int64_t)y * B + b] < (int32_t)v) { ok = false; break; }
+              }
+            }
+            if (ok) {
+              const uint32_t bit = 1u << (b & 31);
+              atomicXor(&S.Zwork[v * Bw + (b >> 5)], bit);
+              atomicXor(&S.Zwork[(int64_t)fb * Bw + (b >> 5)], bit);
+              acc3 += 1;
+            }
+          }
+        }
+      } else {
+        // ---------------- pass C: counts of the (new) work set
+        const bool act = round != RD_NONE;
+        const bool zv = get_bit(S.Zwork, v, Bw, b);
+        bool aux = false, fr = false;
+        if (act) {
+          S.owner[e] = 0x7fffffff;
+          if (mis) {
+            int c = 0;
+            for (int32_t j = rs; j < re && c < 2; ++j) c += get_bit(S.Zwork, col[j], Bw, b);
+            acc0 += zv;
+            acc1 += zv && c > 0;
+            fr = !zv && c == 0;
+            acc2 += fr;
+            aux = !zv && c == 1;  // tight
+          } else {
+            int P = 0, W = 0;
+            for (int32_t j = rs; j < re; ++j) {
+              const int w = wts ? (int)wts[j] : 1;
+              W += w;
+              if (get_bit(S.Zwork, col[j], Bw, b)) P += w;
+            }
+            const int as = 2 * P - W;
+            acc0 += zv ? (W - P) : P;
+            const bool fixed = zv ? (as <= -1) : (as >= 0);
+            acc1 += !fixed;
+            const int gn = zv ? as : -as;
+            acc2 += gn > 0;
+            S.gain[e] = gn;
+            aux = gn > 0;
+          }
+        }
+        update_word(S.Zaux, v, Bw, b, B, aux, act);
+        update_word(S.Zfree, v, Bw, b, B, fr, act && mis);
+      }
+    }
+    if (my_b >= 0) {
+      if (acc0) atomicAdd(&s_cnt[4 * my_b + 0], (unsigned long long)acc0);
+      if (acc1) atomicAdd(&s_cnt[4 * my_b + 1], (unsigned long long)acc1);
+      if (acc2) atomicAdd(&s_cnt[4 * my_b + 2], (unsigned long long)acc2);
+      if (acc3) atomicAdd(&s_cnt[4 * my_b + 3], (unsigned long long)acc3);
+    }
+    flush_counters(S, s_cnt, item.g, B, S.cnt);
+  }
+}
+
+cudaError_t launch_disc(const SolverDev& S, int pass, int grid, cudaStream_t stream) {
+  k_disc<<<grid, kPairThreads, 0, stream>>>(S, pass);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- readouts
+__global__ void __launch_bounds__(kPairThreads) k_round_bits(SolverDev S, uint32_t* z) {
+  const int64_t t = *S.tick;
+  const void* Xc = (t & 1) ? S.X1 : S.X0;
+  const bool mis = S.p.problem == PROB_MIS;
+  const float thr = mis ? 0.5f : 0.0f;
+  for_pairs(S, nullptr, 0, [&](int g, int64_t v, int b, int64_t tau, bool in) {
+    float x = 0.0f;
+    if (in) {
+      const int64_t e = v * S.B + b;
+      if (S.p.x_dtype == DT_F32) x = static_cast<const float*>(Xc)[e];
+      else if (S.p.x_dtype == DT_BF16) x = __bfloat162float(static_cast<const __nv_bfloat16*>(Xc)[e]);
+      else x = __half2float(static_cast<const __half*>(Xc)[e]);
+    }
+    update_word(z, v, S.Bw, b, S.B, x > thr, in);
+  });
+}
+
+cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, int grid, cudaStream_t stream) {
+  k_round_bits<<<grid, kPairThreads, 0, stream>>>(S, z);
+  return cudaGetLastError();
+}
+
+// exact evaluation of given bits: MIS (size, conflicting edges x2, uncovered);
+// MaxCut (2*cut, non-fixed, positive gain)
+__global__ void __launch_bounds__(kPairThreads) k_eval(SolverDev S, const uint32_t* z, Counters* out) {
+  __shared__ unsigned long long s_cnt[4 * 128];
+  const int B = S.B, Bw = S.Bw;
+  const bool mis = S.p.problem == PROB_MIS;
+  const int32_t* rp = S.g.row_ptr;
+  const int32_t* col = S.g.col;
+  const int8_t* wts = S.g.w;
+  for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
+    const Item item = S.g.items[it];
+    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
+    long long a0 = 0, a1 = 0, a2 = 0;
+    int my_b = -1;
+    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+      const int64_t idx = base + lane;
+      if (idx >= hi) continue;
+      const int64_t v = idx / B;
+      const int b = (int)(idx % B);
+      my_b = b;
+      const bool zv = get_bit(z, v, Bw, b);
+      if (mis) {
+        int c = 0;
+        for (int32_t j = rp[v]; j < rp[v + 1]; ++j) c += get_bit(z, col[j], Bw, b);
+        a0 += zv;
+        a1 += zv ? c : 0;
+        a2 += !zv && c == 0;
+      } else {
+        int P = 0, W = 0;
+        for (int32_t j = rp[v]; j < rp[v + 1]; ++j) {
+          const int w = wts ? (int)wts[j] : 1;
+          W += w;
+          if (get_bit(z, col[j], Bw, b)) P += w;
+        }
+        const int as = 2 * P - W;
+        a0 += zv ? (W - P) : P;
+        a1 += !(zv ? (as <= -1) : (as >= 0));
+        a2 += (zv ? as : -as) > 0;
+      }
+    }
+    if (my_b >= 0) {
+      if (a0) atomicAdd(&s_cnt[4 * my_b + 0], (unsigned long long)a0);
+      if (a1) atomicAdd(&s_cnt[4 * my_b + 1], (unsigned long long)a1);
+      if (a2) atomicAdd(&s_cnt[4 * my_b + 2], (unsigned long long)a2);
+    }
+    flush_counters(S, s_cnt, item.g, B, out);
+  }
+}
+
+cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, int grid, cudaStream_t stream) {
+  k_eval<<<grid, kPairThreads, 0, stream>>>(S, z, out);
+  return cudaGetLastError();
+}
+
+// counters -> user arrays. kind 0: step/machine counters (MaxCut value is 2*cut);
+// kind 1: evaluation counters (MIS a = 2*edges, MaxCut value = 2*cut)
+__global__ void k_counters_out(Counters* c, int64_t T, int mis, int kind, int64_t* value, int64_t* a, int64_t* b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T) return;
+  const Counters x = c[i];
+  int64_t v = (int64_t)x.value, aa = (int64_t)x.a;
+  if (!mis) v /= 2;
+  if (mis && kind == 1) aa /= 2;
+  if (value) value[i] = v;
+  if (a) a[i] = aa;
+  if (b) b[i] = (int64_t)x.b;
+}
+
+cudaError_t launch_counters_out(const SolverDev& S, const Counters* c, int64_t* value, int64_t* a, int64_t* b,
+                                int kind, cudaStream_t stream) {
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  k_counters_out<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(const_cast<Counters*>(c), T,
+                                                                  S.p.problem == PROB_MIS, kind, value, a, b);
+  return cudaGetLastError();
+}
+
+// relaxed objective per trajectory in double: (Ax)_v in float32 (CSR order),
+// then x_v and x_v*(Ax)_v accumulated in double per thread, reduced per
+// item in shared memory
+__global__ void __launch_bounds__(kPairThreads) k_objective(SolverDev S, double* out) {
+  __shared__ double s_obj[128];
+  const int64_t t = *S.tick;
+  const void* Xc = (t & 1) ? S.X1 : S.X0;
+  const int B = S.B;
+  const bool mis = S.p.problem == PROB_MIS;
+  auto ld = [&](int64_t e) -> float {
+    if (S.p.x_dtype == DT_F32) return static_cast<const float*>(Xc)[e];
+    if (S.p.x_dtype == DT_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(Xc)[e]);
+    return __half2float(static_cast<const __half*>(Xc)[e]);
+  };
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_obj[i] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
+    const Item item = S.g.items[it];
+    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
+    double part = 0.0;
+    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+      const int64_t idx = base + lane;
+      if (idx >= hi) continue;
+      const int64_t v = idx / B;
+      const int b = (int)(idx % B);
+      float acc = 0.0f;
+      for (int32_t j = S.g.row_ptr[v]; j < S.g.row_ptr[v + 1]; ++j) {
+        const float xu = ld((int64_t)S.g.col[j] * B + b);
+        if (S.g.w == nullptr || S.g.w[j] >= 0) acc = acc + xu;
+        else acc = acc - xu;
+      }
+      const double xv = (double)ld(v * B + b);
+      part += mis ? xv - 0.5 * (double)S.p.gamma * xv * (double)acc
+                  : -(double)S.p.lambda_ * xv - xv * (double)acc;
+    }
+    if (part != 0.0) atomicAdd(&s_obj[threadIdx.x % B], part);
+    __syncthreads();
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+      if (s_obj[i] != 0.0) atomicAdd(&out[(int64_t)item.g * B + i], s_obj[i]);
+      s_obj[i] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_objective(const SolverDev& S, double* out, int grid, cudaStream_t stream) {
+  k_objective<<<grid, kPairThreads, 0, stream>>>(S, out);
+  return cudaGetLastError();
+}
+
+// after a standalone local search: restore the machine state, keep best
+__global__ void k_ls_merge(TrajState* st, const TrajState* saved, int64_t T) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T) return;
+  TrajState s = saved[i];
+  s.best = st[i].best;
+  s.accepts = st[i].accepts;
+  st[i] = s;
+}
+
+cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStream_t stream) {
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  k_ls_merge<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(S.st, saved, T);
+  return cudaGetLastError();
+}
+
+}  // namespace mqo
+
+namespace mqo {
+
+// fresh machine state for every trajectory: first descent of outer
+// iteration 0, no best set; the apply pass then writes the initial x
+__global__ void k_state_init(SolverDev S) {
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  const int64_t tau = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = *S.tick;
+  if (tau < T) {
+    TrajState st;
+    st.phase = PH_DESCENT;
+    st.s = 0;
+    st.r = 0;
+    st.o = 0;
+    st.best = (int64_t)(-9223372036854775807LL - 1);
+    st.ticks = 0;
+    st.last_round = RD_NONE;
+    st.round = RD_NONE;
+    st.last_commits = 0;
+    st.ev_value = st.ev_a = st.ev_b = 0;
+    st.accepts = st.descents = 0;
+    st.act = ACT_INIT;
+    st.ls_done = 0;
+    for (int i = 0; i < 6; ++i) st.rkeys[i] = 0u;
+    st.rk = 0;
+    S.st[tau] = st;
+    S.cnt[tau] = Counters{0ull, 0ull, 0ull, 0ull};
+    const int g = (int)(tau / S.B);
+    S.gflag[g] = (int32_t)(t + 1);
+  }
+  if (tau == 0) S.any[0] = (int32_t)(t + 1);
+}
+
+cudaError_t launch_state_init(const SolverDev& S, cudaStream_t stream) {
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  k_state_init<<<(unsigned)((T + 127) / 128), 128, 0, stream>>>(S);
+  return cudaGetLastError();
+}
+
+// out = number of trajectories still running a standalone local search
+__global__ void k_any_pending(SolverDev S, int32_t* out) {
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  int c = 0;
+  for (int64_t i = threadIdx.x; i < T; i += blockDim.x) c += S.st[i].ls_done == 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ int s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += s[i];
+    *out = tot;
+  }
+}
+
+cudaError_t launch_any_pending(const SolverDev& S, int32_t* out, cudaStream_t stream) {
+  k_any_pending<<<1, 1024, 0, stream>>>(S, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mqo
