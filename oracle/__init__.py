@@ -87,6 +87,7 @@ def lib():
             _lib.orc_eval_mis.argtypes = [P, P, P]
             _lib.orc_eval_cut.argtypes = [P, P, P]
             _lib.orc_descent_step.argtypes = [P, P, P, P, P, P, P, P]
+            _lib.orc_step_rows.argtypes = [P, P, P, P, P, C.c_int64, P, P]
             for nm in ("orc_round_drop", "orc_round_complete", "orc_round_swap", "orc_round_flip1",
                        "orc_round_flip2"):
                 getattr(_lib, nm).restype = C.c_int64
@@ -190,6 +191,16 @@ def descent_step(g: Graph, p, x, V):
     ev = np.zeros(4, dtype=np.int64)
     lib().orc_descent_step(g.ref(), C.byref(p), _ptr(x), _ptr(V), _ptr(xn), _ptr(Vn), _ptr(z), _ptr(ev))
     return xn, Vn, z, tuple(int(v) for v in ev[:3])
+
+
+def step_rows(g: Graph, p, x, V, rows):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    xn = np.zeros(len(rows), dtype=np.float32)
+    Vn = np.zeros(len(rows), dtype=np.float32)
+    lib().orc_step_rows(g.ref(), C.byref(p), _ptr(x), _ptr(V), _ptr(rows), len(rows), _ptr(xn), _ptr(Vn))
+    return xn, Vn
 
 
 def _round(name, g: Graph, z):

@@ -403,6 +403,37 @@ ORC_API void orc_descent_step(const orc_graph* g, const orc_params* p, const flo
   }
 }
 
+/* The same step restricted to the listed rows (for sampled checks on
+ * graphs too large to step whole): x_new[k], V_new[k] for row rows[k]. */
+ORC_API void orc_step_rows(const orc_graph* g, const orc_params* p, const float* x, const float* V,
+                           const int64_t* rows, int64_t k, float* x_new, float* V_new) {
+  float lo, hi;
+  box(p, &lo, &hi);
+  for (int64_t i = 0; i < k; ++i) {
+    int64_t v = rows[i];
+    float acc = 0.0f;
+    for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) {
+      float xu = x[g->col[j]];
+      if (wt(g, j) >= 0) acc = acc + xu;
+      else acc = acc - xu;
+    }
+    float grad;
+    if (p->problem == ORC_MIS) {
+      float t = p->gamma * acc;
+      grad = 1.0f - t;
+    } else {
+      float t = 2.0f * acc;
+      grad = -p->lambda_ - t;
+    }
+    float a = p->momentum * V[v];
+    float b = p->alpha * grad;
+    float vn = a + b;
+    float xn = clampf(x[v] + vn, lo, hi);
+    V_new[i] = orc_round_store(vn, p->v_dtype);
+    x_new[i] = orc_round_store(xn, p->x_dtype);
+  }
+}
+
 /* ------------------------------------------------------------------ */
 /* Discrete rounds.  Every decision in a round reads the snapshot of z   */
 /* taken at the start of the round; the moves are applied afterwards.    */

@@ -698,10 +698,20 @@ mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
   if (!out) return fail(MQO_EINVAL, "null out");
   const size_t T = (size_t)s->S.g.num_graphs * s->S.B;
   std::vector<TrajState> h(T);
+  std::vector<Counters> c(T);
   CKS(cudaStreamSynchronize(s->user));
   CKS(cudaStreamSynchronize(s->work));
   CKS(cudaMemcpy(h.data(), s->S.st, T * sizeof(TrajState), cudaMemcpyDeviceToHost));
+  CKS(cudaMemcpy(c.data(), s->S.cnt, T * sizeof(Counters), cudaMemcpyDeviceToHost));
+  const bool mis = s->p.problem == MQO_MIS;
   for (size_t i = 0; i < T; ++i) {
+    // the counters of the last tick are folded into the state by the next
+    // control pass; report them as the latest evaluation
+    const int64_t cv = (int64_t)c[i].value;
+    h[i].ev_value = mis ? cv : cv / 2;
+    h[i].ev_a = (int64_t)c[i].a;
+    h[i].ev_b = (int64_t)c[i].b;
+    h[i].last_commits = (int64_t)c[i].commits;
     mqo_traj_info& o = out[i];
     const TrajState& t = h[i];
     o.phase = t.phase;

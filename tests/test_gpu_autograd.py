@@ -1,0 +1,126 @@
+"""f_B as a differentiable objective: forward, fused-SpMM backward, optimisers.
+
+The backward (grad f_B = -lambda 1 - 2 A x, proof of Thm 3.6) is checked
+against the oracle's float64 gradient, against central finite differences
+(h = 1e-3) and through torch.autograd; the projected momentum / Adam kernels
+against torch.optim's SGD(momentum) / Adam followed by a clamp.
+"""
+import numpy as np
+import pytest
+
+import mqo_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mq():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2605_06921_gb300 as m
+    return m
+
+
+def power_law_with_hub(n=20000, hub=3000, seed=0):
+    """Chung–Lu graph plus a star whose centre has degree > the chunk split."""
+    cl = mi.chung_lu(n, 2.5, 8.0, seed)
+    star = mi.from_edges(hub + 1, np.zeros(hub, int), np.arange(1, hub + 1))
+    G = mi.pack([cl, star])
+    return mi.Graph(G.n, G.row_ptr, G.col_idx, None)  # one graph (block diagonal)
+
+
+@pytest.fixture(scope="module")
+def graph_and_x():
+    G = power_law_with_hub()
+    rng = np.random.default_rng(0)
+    B = 8
+    X = (rng.random((G.n, B)) * 2 - 1).astype(np.float32)
+    return G, X, B
+
+
+def test_forward_matches_oracle(mq, graph_and_x):
+    G, X, B = graph_and_x
+    assert G.degrees().max() > 512  # chunked rows are exercised
+    g = mq.Graph(G)
+    lam = 0.001
+    obj = mq.fb_forward(g, torch.from_numpy(X).cuda(), lam).cpu().numpy()
+    og = oracle.Graph(G)
+    for b in range(B):
+        want = oracle.objective_f64(og, oracle.MAXCUT, 0.0, lam, X[:, b].astype(np.float64))
+        assert obj[b] == pytest.approx(want, rel=2e-6, abs=1e-3)
+
+
+def test_backward_matches_oracle_gradient(mq, graph_and_x):
+    G, X, B = graph_and_x
+    g = mq.Graph(G)
+    lam = 0.001
+    gout = torch.linspace(0.5, 2.0, B, device="cuda")
+    Gr = mq.spmm_grad(g, torch.from_numpy(X).cuda(), lam, gout).cpu().numpy()
+    og = oracle.Graph(G)
+    go = gout.cpu().numpy().astype(np.float64)
+    for b in range(B):
+        want = go[b] * oracle.gradient_f64(og, oracle.MAXCUT, 0.0, lam, X[:, b].astype(np.float64))
+        assert np.allclose(Gr[:, b], want, rtol=1e-5, atol=1e-4)
+
+
+def test_backward_central_differences(mq, graph_and_x):
+    G, X, B = graph_and_x
+    g = mq.Graph(G)
+    lam = 0.001
+    rng = np.random.default_rng(1)
+    Xt = torch.from_numpy(X).cuda()
+    Gr = mq.spmm_grad(g, Xt, lam).double()
+    og = oracle.Graph(G)
+    h = 1e-3
+    for _ in range(3):
+        D = torch.from_numpy(rng.standard_normal(X.shape).astype(np.float32)).cuda()
+        want = (Gr * D.double()).sum(dim=0).cpu().numpy()
+        Xp = (Xt.double() + h * D.double()).cpu().numpy()
+        Xm = (Xt.double() - h * D.double()).cpu().numpy()
+        for b in range(B):
+            fd = (oracle.objective_f64(og, 1, 0.0, lam, Xp[:, b]) - oracle.objective_f64(og, 1, 0.0, lam, Xm[:, b])) / (2 * h)
+            assert fd == pytest.approx(want[b], rel=1e-5, abs=1e-3)
+        # the GPU forward's own finite differences (float32 terms, double sums)
+        fp = mq.fb_forward(g, (Xt + h * D).contiguous(), lam).cpu().numpy()
+        fm = mq.fb_forward(g, (Xt - h * D).contiguous(), lam).cpu().numpy()
+        assert np.allclose((fp - fm) / (2 * h), want, rtol=2e-2, atol=1.0)
+
+
+def test_autograd_function(mq, graph_and_x):
+    G, X, B = graph_and_x
+    g = mq.Graph(G)
+    lam = 0.002
+    Xt = torch.from_numpy(X).cuda().requires_grad_(True)
+    w = torch.arange(1, B + 1, device="cuda", dtype=torch.float64)
+    loss = (mq.FbObjective.apply(Xt, g, lam) * w).sum()
+    loss.backward()
+    want = mq.spmm_grad(g, Xt.detach(), lam, w.float())
+    assert torch.equal(Xt.grad, want)
+
+
+def test_momentum_and_adam_match_torch(mq, graph_and_x):
+    G, X, B = graph_and_x
+    g = mq.Graph(G)
+    lam = 0.001
+    x0 = torch.from_numpy(X).cuda()
+    for kind in ("momentum", "adam"):
+        xa = x0.clone().requires_grad_(True)
+        xb = x0.clone().requires_grad_(True)
+        if kind == "momentum":
+            oa = mq.PGAMomentum([xa], lr=0.003, momentum=0.8)
+            ob = torch.optim.SGD([xb], lr=0.003, momentum=0.8)
+        else:
+            oa = mq.PGAAdam([xa], lr=0.01)
+            ob = torch.optim.Adam([xb], lr=0.01)
+        for _ in range(5):
+            oa.zero_grad()
+            mq.FbObjective.apply(xa, g, lam).sum().backward()
+            oa.step()
+            ob.zero_grad()
+            xb.grad = -mq.spmm_grad(g, xb.detach(), lam)  # torch minimises -f
+            ob.step()
+            with torch.no_grad():
+                xb.clamp_(-1.0, 1.0)
+        assert torch.allclose(xa, xb, rtol=1e-5, atol=1e-5), kind

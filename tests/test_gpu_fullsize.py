@@ -1,0 +1,135 @@
+"""Full-size parity on sampled outputs (the oracle replays sampled
+trajectories / rows one by one), in the launch configuration bench.py uses.
+"""
+import numpy as np
+import pytest
+
+import mqo_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mq():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2605_06921_gb300 as m
+    return m
+
+
+def host(t):
+    if t.dtype in (torch.bfloat16, torch.float16):
+        t = t.float()
+    return t.cpu().numpy()
+
+
+def sampled_machine_check(mq, G, p, warm, ticks, samples, timed=True):
+    s = mq.Solver(mq.Graph(G), p)
+    s.run(warm)
+    if timed:
+        ms, launches = s.run_timed(ticks)
+        assert launches == ticks and ms > 0
+    else:
+        s.run(ticks)
+    total = warm + ticks
+    vals, bits = s.best()
+    z = mq.unpack_bits(bits, G.n, p.batch)
+    x = host(s.get_x())
+    states = s.traj_state()
+    po = oracle.params(problem=p.problem, batch=p.batch, x_dtype=p.x_dtype, v_dtype=p.v_dtype, alpha=p.alpha,
+                       momentum=p.momentum, gamma=p.gamma, lambda_=p.lambda_, rho=p.rho, sigma=p.sigma, t_gs=p.t_gs,
+                       descent_cap=p.descent_cap, init_kind=p.init_kind, local_search=p.local_search,
+                       repair=p.repair, seed=p.seed)
+    for g, b in samples:
+        sub = G.subgraph(g)
+        og = oracle.Graph(sub)
+        t = g * p.batch + b
+        tr = oracle.Trajectory(og, po, t)
+        tr.run(total)
+        lo, hi = int(G.node_offsets[g]), int(G.node_offsets[g + 1])
+        for key in ("phase", "s", "r", "o", "best", "ticks", "ev_value", "ev_a", "ev_b", "accepts", "descents"):
+            assert states[t][key] == tr.state[key], (g, b, key, states[t][key], tr.state[key])
+        assert vals[t] == tr.state["best"]
+        assert np.array_equal(z[lo:hi, b], tr.zbest)
+        if tr.state["phase"] == oracle.PH_DESCENT:
+            assert np.array_equal(x[lo:hi, b], tr.x)
+    return s
+
+
+def test_mis_batched_full_size(mq):
+    """512 ER graphs (n ~ U[700,800], p = 0.15), B = 32, BF16 state: the bench workload."""
+    import bench
+    wl = bench.WORKLOADS["mis_batched"]
+    G = mi.workload_mis_batched()
+    p = mq.params(problem=0, batch=32, x_dtype=1, v_dtype=1, alpha=wl["alpha"], momentum=wl["momentum"],
+                  gamma=wl["gamma"], rho=wl["rho"], t_gs=wl["t_gs"], descent_cap=wl["descent_cap"],
+                  init_kind=wl["init_kind"], sigma=wl["sigma"], seed=0)
+    rng = np.random.default_rng(0)
+    samples = [(0, 0), (511, 31)] + [(int(rng.integers(512)), int(rng.integers(32))) for _ in range(6)]
+    sampled_machine_check(mq, G, p, 20, 80, samples)
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_maxcut_regular_full_size(mq, signed):
+    """random 3-regular n = 100,000, B = 128, BF16 state (± weights variant)."""
+    G = mi.workload_maxcut_regular(signed=signed)
+    p = mq.params(problem=1, batch=128, x_dtype=1, v_dtype=1, alpha=0.0025, momentum=0.8, lambda_=0.001, rho=0.8,
+                  t_gs=90, descent_cap=200, init_kind=1, sigma=0.1, seed=1)
+    sampled_machine_check(mq, G, p, 10, 150, [(0, 0), (0, 77), (0, 127)])
+
+
+def test_mis_scale_full_size_one_step(mq):
+    """ER n = 10^7, mean degree 10, B = 16, FP16 state: sampled rows of one
+    fused step and the exact counters of every trajectory."""
+    G = mi.workload_mis_scale()
+    B = 16
+    p = mq.params(problem=0, batch=B, x_dtype=2, v_dtype=2, alpha=0.8, momentum=0.75, rho=0.5, init_kind=1,
+                  sigma=0.1, seed=2)
+    s = mq.Solver(mq.Graph(G), p)
+    s.step(2)
+    x0 = host(s.get_x())
+    v0 = host(s.get_v())
+    s.step(1)
+    x1 = host(s.get_x())
+    v1 = host(s.get_v())
+    sv, sa, sb = (host(t) for t in s.step_stats())
+    og = oracle.Graph(G)
+    po = oracle.params(problem=0, batch=B, x_dtype=2, v_dtype=2, alpha=0.8, momentum=0.75, seed=2)
+    rng = np.random.default_rng(3)
+    rows = np.concatenate([rng.integers(0, G.n, 3000), [0, G.n - 1], np.argsort(G.degrees())[-20:]])
+    for b in range(0, B, 5):
+        xn, vn = oracle.step_rows(og, po, x0[:, b], v0[:, b], rows)
+        assert np.array_equal(x1[rows, b], xn)
+        assert np.array_equal(v1[rows, b], vn)
+        size, ce, cn, unc = oracle.eval_mis(og, (x0[:, b] > 0.5).astype(np.uint8))
+        assert (sv[b], sa[b], sb[b]) == (size, cn, unc)
+
+
+def test_mis_scale_full_size_machine(mq):
+    """ER n = 10^7: a few machine ticks, two trajectories replayed by the oracle."""
+    G = mi.workload_mis_scale()
+    G.node_offsets = np.array([0, G.n], dtype=np.int64)
+    p = mq.params(problem=0, batch=16, x_dtype=2, v_dtype=2, alpha=0.8, momentum=0.75, rho=0.5, t_gs=60,
+                  descent_cap=12, init_kind=1, sigma=0.1, seed=4)
+    sampled_machine_check(mq, G, p, 0, 30, [(0, 0), (0, 13)])
+
+
+def test_chung_lu_full_size_autograd(mq):
+    """Chung–Lu n = 10^6 (exponent 2.5, mean degree 8), B = 64, FP32."""
+    G = mi.workload_chung_lu()
+    B = 64
+    g = mq.Graph(G)
+    rng = np.random.default_rng(5)
+    X = (rng.random((G.n, B)) * 2 - 1).astype(np.float32)
+    Xt = torch.from_numpy(X).cuda()
+    lam = 0.001
+    obj = mq.fb_forward(g, Xt, lam).cpu().numpy()
+    Gr = mq.spmm_grad(g, Xt, lam).cpu().numpy()
+    og = oracle.Graph(G)
+    for b in (0, 31, 63):
+        xb = X[:, b].astype(np.float64)
+        assert obj[b] == pytest.approx(oracle.objective_f64(og, 1, 0.0, lam, xb), rel=1e-5)
+        want = oracle.gradient_f64(og, 1, 0.0, lam, xb)
+        assert np.allclose(Gr[:, b], want, rtol=1e-5, atol=2e-4)
