@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -32,8 +33,9 @@ mqo_status fail(mqo_status st, const char* fmt, ...) {
   return st;
 }
 
-constexpr int kChunkNodes = 512;  // nodes per item
+constexpr int kChunkNodes = 256;  // nodes per item
 constexpr int kSplit = 512;       // row length above which the f_B kernels chunk a row
+constexpr size_t kStepSmemLimit = 110 * 1024;  // shared-memory step kernel if the graph block fits
 
 }  // namespace
 
@@ -54,6 +56,8 @@ struct mqo_graph_s {
   Item* d_items = nullptr;
   int32_t num_items = 0;
   std::vector<int32_t> h_rp;
+  std::vector<int32_t> h_off;
+  std::vector<Item> h_items;
   // f_B kernels: chunk plan of long rows and their scratch
   bool hp_built = false;
   HeavyPlan hp{};
@@ -88,9 +92,9 @@ struct mqo_solver_s {
   cudaGraphExec_t gx1 = nullptr, gx16 = nullptr;
   bool poisoned = false;
   int grid = 1;
+  size_t step_smem = 0;  // > 0: shared-memory step kernel with this much dynamic smem
   int64_t host_tick = 0;
   Counters* d_cnt_plain = nullptr;
-  uint32_t* d_zplain = nullptr;
   Counters* d_eval = nullptr;
   int32_t* h_pending = nullptr;  // pinned
   int32_t* d_pending = nullptr;
@@ -215,6 +219,8 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
     }
   }
   g->num_items = (int32_t)items.size();
+  g->h_items = items;
+  g->h_off = off32;
   auto cleanup = [&](mqo_status s) {
     mqo_graph_destroy(g);
     return s;
@@ -313,10 +319,10 @@ cudaError_t enqueue_tick(mqo_solver s) {
   const SolverDev& S = s->S;
   const int G = S.g.num_graphs;
   if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
-  if ((e = launch_apply(S, s->grid, s->work)) != cudaSuccess) return e;
-  if ((e = launch_step(S, S.ZXP, S.cnt, S.st, S.gflag + 2 * G, s->grid, s->work)) != cudaSuccess) return e;
+  if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
+  if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work)) != cudaSuccess) return e;
   for (int pass = 0; pass < 3; ++pass)
-    if ((e = launch_disc(S, pass, s->grid, s->work)) != cudaSuccess) return e;
+    if ((e = launch_disc(S, pass, s->work)) != cudaSuccess) return e;
   return launch_tick_end(S, s->work);
 }
 
@@ -324,9 +330,9 @@ cudaError_t enqueue_ls_tick(mqo_solver s, int mode) {
   cudaError_t e;
   const SolverDev& S = s->S;
   if ((e = launch_ctrl(S, mode, nullptr, s->work)) != cudaSuccess) return e;
-  if ((e = launch_apply(S, s->grid, s->work)) != cudaSuccess) return e;
+  if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
   for (int pass = 0; pass < 3; ++pass)
-    if ((e = launch_disc(S, pass, s->grid, s->work)) != cudaSuccess) return e;
+    if ((e = launch_disc(S, pass, s->work)) != cudaSuccess) return e;
   return launch_tick_end(S, s->work);
 }
 
@@ -454,16 +460,36 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
   S.X0 = x0;
   S.X1 = x1;
   S.V = vv;
-  uint32_t** wbufs[] = {&S.ZXP, &S.Zbest, &S.Zwork, &S.Zaux, &S.Zfree, &S.Zdrop, &s->d_zplain};
+  uint32_t** wbufs[] = {&S.ZX0, &S.ZX1, &S.Zbest, &S.Zwork, &S.Zaux, &S.Zfree, &S.Zdrop};
   for (auto pp : wbufs)
     if ((st = dalloc(pp, s->words, &s->allocs)) != MQO_OK) return bail(st);
   int32_t** ibufs[] = {&S.owner, &S.pa, &S.pb, &S.gain};
   for (auto pp : ibufs)
     if ((st = dalloc(pp, s->pairs, &s->allocs)) != MQO_OK) return bail(st);
+  // counter replicas: enough that one replica sees at most ~8 items of a graph
+  {
+    int max_items = 1, max_ng = 1;
+    std::vector<int32_t> per(g->G, 0);
+    for (const Item& it : g->h_items) per[it.g] += 1;
+    for (int32_t k = 0; k < g->G; ++k) max_items = std::max(max_items, per[k]);
+    for (int32_t k = 0; k < g->G; ++k) max_ng = std::max(max_ng, g->h_off[k + 1] - g->h_off[k]);
+    int R = 1;
+    while (R < 64 && R * 8 < max_items) R *= 2;
+    S.R = R;
+    const size_t need = step_smem_bytes(B, p->x_dtype, p->problem, max_ng);
+    // MQO_STEP_KERNEL=generic selects the global-memory step kernel even
+    // when the member graphs fit in shared memory
+    const char* force = getenv("MQO_STEP_KERNEL");
+    const bool generic = force && strcmp(force, "generic") == 0;
+    s->step_smem = (!generic && B >= 32 && need <= kStepSmemLimit) ? need : 0;
+  }
+  const size_t TR = (size_t)T * S.R;
   if ((st = dalloc(&S.st, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
-  if ((st = dalloc(&S.cnt, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
-  if ((st = dalloc(&s->d_cnt_plain, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
-  if ((st = dalloc(&s->d_eval, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.act, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.rnd, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.cnt, TR, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&s->d_cnt_plain, TR, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&s->d_eval, TR, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.tick, 1, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.gflag, (size_t)3 * g->G, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.any, 4, &s->allocs)) != MQO_OK) return bail(st);
@@ -505,15 +531,15 @@ mqo_status mqo_init(mqo_solver s) {
   Scope sc(s);
   SolverDev& S = s->S;
   CKS(cudaMemsetAsync(S.V, 0, s->v_bytes, s->work));
-  for (uint32_t* w : {S.ZXP, S.Zbest, S.Zwork, S.Zaux, S.Zfree, S.Zdrop, s->d_zplain})
+  for (uint32_t* w : {S.ZX0, S.ZX1, S.Zbest, S.Zwork, S.Zaux, S.Zfree, S.Zdrop})
     CKS(cudaMemsetAsync(w, 0, s->words * sizeof(uint32_t), s->work));
   CKS(cudaMemsetAsync(S.owner, 0x7f, s->pairs * sizeof(int32_t), s->work));
   CKS(cudaMemsetAsync(S.pa, 0xff, s->pairs * sizeof(int32_t), s->work));
   CKS(cudaMemsetAsync(S.pb, 0xff, s->pairs * sizeof(int32_t), s->work));
   CKS(cudaMemsetAsync(S.gain, 0, s->pairs * sizeof(int32_t), s->work));
-  CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B, s->work));
+  CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B * S.R, s->work));
   CKS(launch_state_init(S, s->work));
-  CKS(launch_apply(S, s->grid, s->work));
+  CKS(launch_apply(S, s->work));
   return MQO_OK;
 }
 
@@ -547,11 +573,11 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* step_ms, int64_t*
     const int G = S.g.num_graphs;
     for (int64_t k = 0; k < nticks && err == cudaSuccess; ++k) {
       err = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
-      if (err == cudaSuccess) err = launch_apply(S, s->grid, s->work);
+      if (err == cudaSuccess) err = launch_apply(S, s->work);
       if (err == cudaSuccess) err = cudaEventRecord(ev[(size_t)2 * k], s->work);
-      if (err == cudaSuccess) err = launch_step(S, S.ZXP, S.cnt, S.st, S.gflag + 2 * G, s->grid, s->work);
+      if (err == cudaSuccess) err = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
       if (err == cudaSuccess) err = cudaEventRecord(ev[(size_t)2 * k + 1], s->work);
-      for (int pass = 0; pass < 3 && err == cudaSuccess; ++pass) err = launch_disc(S, pass, s->grid, s->work);
+      for (int pass = 0; pass < 3 && err == cudaSuccess; ++pass) err = launch_disc(S, pass, s->work);
       if (err == cudaSuccess) err = launch_tick_end(S, s->work);
     }
   }
@@ -582,8 +608,8 @@ mqo_status mqo_step(mqo_solver s, int32_t nsteps) {
   Scope sc(s);
   const SolverDev& S = s->S;
   for (int32_t i = 0; i < nsteps; ++i) {
-    CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B, s->work));
-    CKS(launch_step(S, s->d_zplain, s->d_cnt_plain, nullptr, nullptr, s->grid, s->work));
+    CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B * S.R, s->work));
+    CKS(launch_step(S, s->d_cnt_plain, nullptr, nullptr, s->step_smem, s->work));
     CKS(launch_tick_end(S, s->work));
   }
   s->host_tick += nsteps;
@@ -601,7 +627,7 @@ mqo_status mqo_reset(mqo_solver s, const uint8_t* traj_mask) {
   CHECK_SOLVER(s);
   Scope sc(s);
   CKS(launch_ctrl(s->S, CTRL_RESET, traj_mask, s->work));
-  CKS(launch_apply(s->S, s->grid, s->work));
+  CKS(launch_apply(s->S, s->work));
   return MQO_OK;
 }
 
@@ -609,7 +635,7 @@ mqo_status mqo_round(mqo_solver s, uint32_t* z_bits) {
   CHECK_SOLVER(s);
   if (!z_bits) return fail(MQO_EINVAL, "null z_bits");
   Scope sc(s);
-  CKS(launch_round_bits(s->S, z_bits, s->grid, s->work));
+  CKS(launch_round_bits(s->S, z_bits, s->work));
   return MQO_OK;
 }
 
@@ -619,8 +645,8 @@ mqo_status mqo_evaluate(mqo_solver s, const uint32_t* z_bits, int64_t* value, in
   if (!z_bits) return fail(MQO_EINVAL, "null z_bits");
   Scope sc(s);
   const SolverDev& S = s->S;
-  CKS(cudaMemsetAsync(s->d_eval, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B, s->work));
-  CKS(launch_eval(S, z_bits, s->d_eval, s->grid, s->work));
+  CKS(cudaMemsetAsync(s->d_eval, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B * S.R, s->work));
+  CKS(launch_eval(S, z_bits, s->d_eval, s->work));
   CKS(launch_counters_out(S, s->d_eval, value, conflicts, uncovered, 1, s->work));
   return MQO_OK;
 }
@@ -632,7 +658,8 @@ mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds) {
   SolverDev& S = s->S;
   const size_t T = (size_t)S.g.num_graphs * S.B;
   const size_t wb = s->words * sizeof(uint32_t), pbytes = s->pairs * sizeof(int32_t);
-  const size_t save_bytes = T * sizeof(TrajState) + T * sizeof(Counters) + 4 * wb + 4 * pbytes;
+  const size_t TR = T * (size_t)S.R;
+  const size_t save_bytes = T * sizeof(TrajState) + TR * sizeof(Counters) + 4 * wb + 4 * pbytes;
   if (!s->d_save) CKS(cudaMalloc(&s->d_save, save_bytes));
   char* q = static_cast<char*>(s->d_save);
   TrajState* sv_st = reinterpret_cast<TrajState*>(q);
@@ -642,8 +669,8 @@ mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds) {
     void* src;
     size_t n;
   };
-  std::vector<Pair> saves = {{q, S.cnt, T * sizeof(Counters)}};
-  q += T * sizeof(Counters);
+  std::vector<Pair> saves = {{q, S.cnt, TR * sizeof(Counters)}};
+  q += TR * sizeof(Counters);
   for (uint32_t* w : {S.Zwork, S.Zaux, S.Zfree, S.Zdrop}) {
     saves.push_back({q, w, wb});
     q += wb;
@@ -698,20 +725,28 @@ mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
   if (!out) return fail(MQO_EINVAL, "null out");
   const size_t T = (size_t)s->S.g.num_graphs * s->S.B;
   std::vector<TrajState> h(T);
-  std::vector<Counters> c(T);
+  const int R = s->S.R;
+  std::vector<Counters> c(T * R);
   CKS(cudaStreamSynchronize(s->user));
   CKS(cudaStreamSynchronize(s->work));
   CKS(cudaMemcpy(h.data(), s->S.st, T * sizeof(TrajState), cudaMemcpyDeviceToHost));
-  CKS(cudaMemcpy(c.data(), s->S.cnt, T * sizeof(Counters), cudaMemcpyDeviceToHost));
+  CKS(cudaMemcpy(c.data(), s->S.cnt, T * R * sizeof(Counters), cudaMemcpyDeviceToHost));
   const bool mis = s->p.problem == MQO_MIS;
   for (size_t i = 0; i < T; ++i) {
     // the counters of the last tick are folded into the state by the next
     // control pass; report them as the latest evaluation
-    const int64_t cv = (int64_t)c[i].value;
+    Counters sum{0ull, 0ull, 0ull, 0ull};
+    for (int r = 0; r < R; ++r) {
+      sum.value += c[i * R + r].value;
+      sum.a += c[i * R + r].a;
+      sum.b += c[i * R + r].b;
+      sum.commits += c[i * R + r].commits;
+    }
+    const int64_t cv = (int64_t)sum.value;
     h[i].ev_value = mis ? cv : cv / 2;
-    h[i].ev_a = (int64_t)c[i].a;
-    h[i].ev_b = (int64_t)c[i].b;
-    h[i].last_commits = (int64_t)c[i].commits;
+    h[i].ev_a = (int64_t)sum.a;
+    h[i].ev_b = (int64_t)sum.b;
+    h[i].last_commits = (int64_t)sum.commits;
     mqo_traj_info& o = out[i];
     const TrajState& t = h[i];
     o.phase = t.phase;
@@ -746,7 +781,9 @@ mqo_status mqo_set_x(mqo_solver s, const void* x_in) {
   if (!x_in) return fail(MQO_EINVAL, "null x_in");
   Scope sc(s);
   void* dst = (s->host_tick & 1) ? s->S.X1 : s->S.X0;
+  uint32_t* zdst = (s->host_tick & 1) ? s->S.ZX1 : s->S.ZX0;
   CKS(cudaMemcpyAsync(dst, x_in, s->x_bytes, cudaMemcpyDeviceToDevice, s->work));
+  CKS(launch_round_bits(s->S, zdst, s->work));
   return MQO_OK;
 }
 
@@ -764,7 +801,7 @@ mqo_status mqo_objective_f64(mqo_solver s, double* out) {
   Scope sc(s);
   const size_t T = (size_t)s->S.g.num_graphs * s->S.B;
   CKS(cudaMemsetAsync(out, 0, T * sizeof(double), s->work));
-  CKS(launch_objective(s->S, out, s->grid, s->work));
+  CKS(launch_objective(s->S, out, s->work));
   return MQO_OK;
 }
 

@@ -84,10 +84,12 @@ struct SolverDev {
   GraphDev g;
   Params p;
   int32_t B, Bw;
-  void* X0;
+  int32_t R;        // counter replicas per trajectory (item i adds into replica i % R)
+  void* X0;         // relaxed x: tick t reads X[t&1] and writes X[(t+1)&1]
   void* X1;
-  void* V;
-  uint32_t* ZXP;    // z of the x evaluated by the last descent step
+  void* V;          // momentum
+  uint32_t* ZX0;    // ZX[k] = threshold rounding of X[k], node-major bits
+  uint32_t* ZX1;
   uint32_t* Zbest;  // best set
   uint32_t* Zwork;  // work set of repair / local search
   uint32_t* Zaux;   // tight (MIS) / positive-gain (MaxCut) bits
@@ -98,11 +100,26 @@ struct SolverDev {
   int32_t* pb;      // [n*B] proposal endpoint b
   int32_t* gain;    // [n*B] 1-flip gains (MaxCut)
   TrajState* st;    // [G*B]
-  Counters* cnt;    // [G*B]
+  int32_t* act;     // [G*B] actions of the current tick (compact copy)
+  int32_t* rnd;     // [G*B] discrete round of the current tick (compact copy)
+  Counters* cnt;    // [G*B*R]
   int64_t* tick;    // current tick number
   int32_t* gflag;   // [3*G] tick stamps: any apply / any discrete / any step
   int32_t* any;     // [4] per-tick "any trajectory" stamps (apply, disc, step)
 };
+
+// sum of the R replicas of a trajectory's counters
+__device__ __forceinline__ Counters sum_replicas(const Counters* c, int64_t tau, int R) {
+  Counters s{0ull, 0ull, 0ull, 0ull};
+  for (int r = 0; r < R; ++r) {
+    const Counters x = c[tau * R + r];
+    s.value += x.value;
+    s.a += x.a;
+    s.b += x.b;
+    s.commits += x.commits;
+  }
+  return s;
+}
 
 // --------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11), device version.

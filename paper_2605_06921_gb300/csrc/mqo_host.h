@@ -11,18 +11,19 @@ constexpr int kPairThreads = 256;  // pair kernels: (node, trajectory) per threa
 
 enum CtrlMode : int { CTRL_MACHINE = 0, CTRL_LS_BEGIN = 1, CTRL_LS = 2, CTRL_RESET = 3 };
 
-cudaError_t launch_step(const SolverDev& S, uint32_t* zout, Counters* cnt, const TrajState* st,
-                        const int32_t* gflag_step, int grid, cudaStream_t stream);
+cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, const int32_t* gflag_step,
+                        size_t smem, cudaStream_t stream);
+size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng);
 
 cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream);
-cudaError_t launch_apply(const SolverDev& S, int grid, cudaStream_t stream);
-cudaError_t launch_disc(const SolverDev& S, int pass, int grid, cudaStream_t stream);
+cudaError_t launch_apply(const SolverDev& S, cudaStream_t stream);
+cudaError_t launch_disc(const SolverDev& S, int pass, cudaStream_t stream);
 cudaError_t launch_tick_end(const SolverDev& S, cudaStream_t stream);
-cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, int grid, cudaStream_t stream);
-cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, int grid, cudaStream_t stream);
+cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, cudaStream_t stream);
+cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, cudaStream_t stream);
 cudaError_t launch_counters_out(const SolverDev& S, const Counters* c, int64_t* value, int64_t* a, int64_t* b,
                                 int kind, cudaStream_t stream);
-cudaError_t launch_objective(const SolverDev& S, double* out, int grid, cudaStream_t stream);
+cudaError_t launch_objective(const SolverDev& S, double* out, cudaStream_t stream);
 cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStream_t stream);
 cudaError_t launch_state_init(const SolverDev& S, cudaStream_t stream);
 cudaError_t launch_any_pending(const SolverDev& S, int32_t* out, cudaStream_t stream);

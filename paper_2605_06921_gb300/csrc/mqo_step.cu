@@ -10,12 +10,20 @@
 // incoming point z = [x > 0.5] (MIS) or [x > 0] (MaxCut): set size,
 // conflicting and uncovered nodes (checker, Eq. MIS checking), or cut,
 // nodes violating the f_B fixed-point condition and positive-gain nodes.
+// The rounding of x' is written next to x' (ZX), so the next step and the
+// acceptance of this step's point read it without recomputing.
 //
 // Thread mapping: a row group of LPR = B/VEC lanes handles one node; lane l
 // owns trajectories l*VEC .. l*VEC+VEC-1 and accumulates them sequentially
-// over the row, so every (v,b) sum is in CSR order.  Rows are streamed in
-// items (node ranges inside one member graph); per-item integer counters
-// are reduced in shared memory and flushed with one atomic per trajectory.
+// over the row, so every (v,b) sum is in CSR order.  Column indices are
+// loaded LPR at a time with one coalesced load and broadcast by shuffles.
+// One CTA per item (a range of at most 256 nodes of one member graph).
+//
+// k_step_g: generic; neighbour rows of x are gathered from global memory.
+// k_step_s: member graphs small enough for shared memory: the CTA first
+//   copies its graph's block of x (and, for MIS, of the rounding bits) to
+//   shared memory; every neighbour gather then hits shared memory, and the
+//   MIS checker ORs whole 32-trajectory words of neighbour bits.
 #include "mqo_dev.cuh"
 #include "mqo_host.h"
 
@@ -23,24 +31,104 @@ namespace mqo {
 
 struct StepArgs {
   GraphDev g;
-  int32_t B, Bw, problem;
+  int32_t B, Bw, R, problem;
   float alpha, momentum, gamma, lambda_;
-  const void* X0;      // x buffers: tick t reads X[t&1], writes X[(t+1)&1]
+  void* X0;
   void* X1;
-  void* V;             // momentum (read/write)
-  uint32_t* zout;      // z of the current x, node-major bits
-  Counters* cnt;       // per-trajectory counters
-  const TrajState* st; // nullptr: every trajectory steps
-  const int32_t* gflag_step;
+  void* V;
+  uint32_t* ZX0;
+  uint32_t* ZX1;
+  Counters* cnt;
+  const int32_t* act;         // nullptr: every trajectory steps
+  const int32_t* gflag_step;  // nullptr: every member graph
   const int64_t* tick;
 };
 
-template <typename TX, typename TV, int VEC>
-__global__ void __launch_bounds__(256) k_step(StepArgs a) {
-  extern __shared__ unsigned long long smem_u64[];
+// Per-element tail of the step: evaluation of z(x), momentum update,
+// projection, storage rounding.  `nb` is the neighbour information of the
+// element: MIS any-neighbour-in-set flag, MaxCut weighted count P of
+// neighbours with z = 1 (wsum = weighted degree).
+template <typename TX, typename TV>
+__device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float thr, float lo, TX xin, TV vin,
+                                             float acc, int nb, int wsum, bool stepping, TX& xout, TV& vout,
+                                             bool& znew, int& c0, int& c1, int& c2) {
+  const float x = to_f(xin);
+  const float vold = to_f(vin);
+  const bool z = x > thr;
+  if (mis) {
+    const bool any = nb != 0;
+    c0 += z;
+    c1 += z && any;
+    c2 += !z && !any;
+  } else {
+    const int as = 2 * nb - wsum;
+    c0 += z ? (wsum - nb) : nb;
+    const bool fixed = z ? (as <= -1) : (as >= 0);
+    c1 += !fixed;
+    const int gn = z ? as : -as;
+    c2 += gn > 0;
+  }
+  float grad;
+  if (mis) {
+    const float tt = a.gamma * acc;
+    grad = 1.0f - tt;
+  } else {
+    const float tt = 2.0f * acc;
+    grad = -a.lambda_ - tt;
+  }
+  const float m1 = a.momentum * vold;
+  const float m2 = a.alpha * grad;
+  const float vn = m1 + m2;
+  const float xn = clamp_box(x + vn, lo, 1.0f);
+  if (stepping) {
+    xout = from_f<TX>(xn);
+    vout = from_f<TV>(vn);
+  } else {
+    xout = xin;
+    vout = vin;
+  }
+  znew = to_f(xout) > thr;
+}
+
+// flush per-lane counters of an item: shared-memory reduction, then one
+// atomic per trajectory and counter into replica (item % R)
+template <int VEC>
+__device__ __forceinline__ void flush_step_counters(const StepArgs& a, unsigned long long* s_cnt, int g, int it,
+                                                    int b0, const int* c0, const int* c1, const int* c2,
+                                                    const bool* stepping) {
   const int B = a.B;
-  unsigned long long* s_cnt = smem_u64;              // [B][3]
-  int* s_step = reinterpret_cast<int*>(s_cnt + 3 * B);  // [B]
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    if (!stepping[e]) continue;
+    if (c0[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 0], (unsigned long long)(long long)c0[e]);
+    if (c1[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 1], (unsigned long long)(long long)c1[e]);
+    if (c2[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 2], (unsigned long long)(long long)c2[e]);
+  }
+  __syncthreads();
+  const int rep = it % a.R;
+  for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) {
+    const unsigned long long val = s_cnt[i];
+    if (val) {
+      const int bb = i / 3, k = i - 3 * bb;
+      Counters* c = a.cnt + ((int64_t)g * B + bb) * a.R + rep;
+      unsigned long long* dst = k == 0 ? &c->value : (k == 1 ? &c->a : &c->b);
+      atomicAdd(dst, val);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- generic
+template <typename TX, typename TV, int VEC>
+__global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
+  __shared__ unsigned long long s_cnt[3 * 128];
+  const int it = blockIdx.x;
+  const Item item = a.g.items[it];
+  const int g = item.g;
+  const int64_t t = *a.tick;
+  if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
+  const int B = a.B;
+  for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  __syncthreads();
 
   const int lpr = B / VEC;
   const int rpw = 32 / lpr;
@@ -50,175 +138,283 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a) {
   const int b0 = l * VEC;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int64_t t = *a.tick;
   const bool mis = a.problem == PROB_MIS;
   const float thr = mis ? 0.5f : 0.0f;
   const float lo = mis ? 0.0f : -1.0f;
   const bool weighted = a.g.w != nullptr;
   const TX* __restrict__ Xc = static_cast<const TX*>((t & 1) ? a.X1 : a.X0);
-  TX* __restrict__ Xn = static_cast<TX*>((t & 1) ? const_cast<void*>(a.X0) : a.X1);
+  TX* __restrict__ Xn = static_cast<TX*>((t & 1) ? a.X0 : a.X1);
+  uint32_t* __restrict__ Zn = (t & 1) ? a.ZX0 : a.ZX1;
   TV* __restrict__ V = static_cast<TV*>(a.V);
   const int32_t* __restrict__ rp = a.g.row_ptr;
   const int32_t* __restrict__ col = a.g.col;
   const int8_t* __restrict__ wts = a.g.w;
-  // lanes sharing one output bit word
-  const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;
+  const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;  // lanes sharing one output bit word
   const unsigned rmask = lpr == 32 ? 0xffffffffu : (((1u << lpr) - 1u) << (sub * lpr));
 
-  for (int it = blockIdx.x; it < a.g.num_items; it += gridDim.x) {
-    const Item item = a.g.items[it];
-    const int g = item.g;
-    if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) continue;
-    for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) s_cnt[i] = 0ull;
-    for (int i = threadIdx.x; i < B; i += blockDim.x)
-      s_step[i] = a.st ? (a.st[(int64_t)g * B + i].act & ACT_STEP) : 1;
-    __syncthreads();
+  bool stepping[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) stepping[e] = a.act ? (a.act[(int64_t)g * B + b0 + e] & ACT_STEP) != 0 : true;
+  int c0[VEC], c1[VEC], c2[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
 
-    bool stepping[VEC];
+  for (int v = item.v0 + warp * rpw + sub; v < item.v1; v += nwarps * rpw) {
+    const int64_t base = (int64_t)v * B + b0;
+    const Pack<TX, VEC> xv = ld_pack<TX, VEC>(Xc + base);
+    const Pack<TV, VEC> vv = ld_pack_stream<TV, VEC>(V + base);
+    float acc[VEC];
+    int pos[VEC];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) stepping[e] = s_step[b0 + e] != 0;
-    int c0[VEC], c1[VEC], c2[VEC];
+    for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
+    const int rs = rp[v], re = rp[v + 1];
+    int wsum = 0;
+    for (int cb = rs; cb < re; cb += lpr) {
+      const int j = cb + l;
+      const int myu = j < re ? __ldcs(col + j) : 0;
+      const int myw = (weighted && j < re) ? (int)wts[j] : 1;
+      const int cnt = min(lpr, re - cb);
+      int k = 0;
+      for (; k + 8 <= cnt; k += 8) {
+        int u[8], w[8];
+        Pack<TX, VEC> p[8];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
-
-    for (int v = item.v0 + warp * rpw + sub; v < item.v1; v += nwarps * rpw) {
-      const int64_t base = (int64_t)v * B + b0;
-      const Pack<TX, VEC> xv = ld_pack<TX, VEC>(Xc + base);
-      const Pack<TV, VEC> vv = ld_pack_stream<TV, VEC>(V + base);
-      float acc[VEC];
-      int pos[VEC];
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
-      const int rs = rp[v], re = rp[v + 1];
-      int wsum = re - rs;
-      if (!weighted) {
-        int j = rs;
-        for (; j + 4 <= re; j += 4) {
-          const int u0 = __ldcs(col + j), u1 = __ldcs(col + j + 1), u2 = __ldcs(col + j + 2),
-                    u3 = __ldcs(col + j + 3);
-          const Pack<TX, VEC> p0 = ld_pack<TX, VEC>(Xc + (int64_t)u0 * B + b0);
-          const Pack<TX, VEC> p1 = ld_pack<TX, VEC>(Xc + (int64_t)u1 * B + b0);
-          const Pack<TX, VEC> p2 = ld_pack<TX, VEC>(Xc + (int64_t)u2 * B + b0);
-          const Pack<TX, VEC> p3 = ld_pack<TX, VEC>(Xc + (int64_t)u3 * B + b0);
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            const float f0 = to_f(p0.e[e]), f1 = to_f(p1.e[e]), f2 = to_f(p2.e[e]), f3 = to_f(p3.e[e]);
-            acc[e] = acc[e] + f0;
-            acc[e] = acc[e] + f1;
-            acc[e] = acc[e] + f2;
-            acc[e] = acc[e] + f3;
-            pos[e] += (f0 > thr) + (f1 > thr) + (f2 > thr) + (f3 > thr);
-          }
+        for (int q = 0; q < 8; ++q) {
+          u[q] = __shfl_sync(rmask, myu, k + q, lpr);
+          w[q] = weighted ? __shfl_sync(rmask, myw, k + q, lpr) : 1;
         }
-        for (; j < re; ++j) {
-          const int u = __ldcs(col + j);
-          const Pack<TX, VEC> p = ld_pack<TX, VEC>(Xc + (int64_t)u * B + b0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = ld_pack<TX, VEC>(Xc + (int64_t)u[q] * B + b0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          wsum += w[q];
 #pragma unroll
           for (int e = 0; e < VEC; ++e) {
-            const float f = to_f(p.e[e]);
-            acc[e] = acc[e] + f;
-            pos[e] += (f > thr);
-          }
-        }
-      } else {
-        wsum = 0;
-        for (int j = rs; j < re; ++j) {
-          const int u = __ldcs(col + j);
-          const int w = wts[j];
-          wsum += w;
-          const Pack<TX, VEC> p = ld_pack<TX, VEC>(Xc + (int64_t)u * B + b0);
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            const float f = to_f(p.e[e]);
-            if (w >= 0) acc[e] = acc[e] + f;
-            else acc[e] = acc[e] - f;
-            pos[e] += (f > thr) ? w : 0;
+            const float f = to_f(p[q].e[e]);
+            acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
+            pos[e] += (f > thr) ? w[q] : 0;
           }
         }
       }
-
-      Pack<TX, VEC> xo;
-      Pack<TV, VEC> vo;
-      unsigned zbits = 0u;
+      for (; k < cnt; ++k) {
+        const int u = __shfl_sync(rmask, myu, k, lpr);
+        const int w = weighted ? __shfl_sync(rmask, myw, k, lpr) : 1;
+        const Pack<TX, VEC> p = ld_pack<TX, VEC>(Xc + (int64_t)u * B + b0);
+        wsum += w;
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) {
-        const float x = to_f(xv.e[e]);
-        const float vold = to_f(vv.e[e]);
-        const bool z = x > thr;
-        zbits |= (unsigned)z << e;
-        if (mis) {
-          const bool any = pos[e] > 0;
-          c0[e] += z;
-          c1[e] += z && any;
-          c2[e] += !z && !any;
-        } else {
-          const int as = 2 * pos[e] - wsum;
-          c0[e] += z ? (wsum - pos[e]) : pos[e];
-          const bool fixed = z ? (as <= -1) : (as >= 0);
-          c1[e] += !fixed;
-          const int gn = z ? as : -as;
-          c2[e] += gn > 0;
+        for (int e = 0; e < VEC; ++e) {
+          const float f = to_f(p.e[e]);
+          acc[e] = w >= 0 ? acc[e] + f : acc[e] - f;
+          pos[e] += (f > thr) ? w : 0;
         }
-        float grad;
-        if (mis) {
-          const float tt = a.gamma * acc[e];
-          grad = 1.0f - tt;
-        } else {
-          const float tt = 2.0f * acc[e];
-          grad = -a.lambda_ - tt;
-        }
-        const float m1 = a.momentum * vold;
-        const float m2 = a.alpha * grad;
-        const float vn = m1 + m2;
-        const float xn = clamp_box(x + vn, lo, 1.0f);
-        xo.e[e] = stepping[e] ? from_f<TX>(xn) : xv.e[e];
-        vo.e[e] = stepping[e] ? from_f<TV>(vn) : vv.e[e];
       }
-      st_pack<TX, VEC>(Xn + base, xo);
-      st_pack<TV, VEC>(V + base, vo);
-      // gather the bits of the lanes sharing this output word
-      unsigned word = zbits << (b0 & 31);
-      for (int off = 1; off < K; off <<= 1) word |= __shfl_xor_sync(rmask, word, off);
-      if ((l % K) == 0) a.zout[(int64_t)v * a.Bw + (b0 >> 5)] = word;
     }
+    Pack<TX, VEC> xo;
+    Pack<TV, VEC> vo;
+    unsigned zbits = 0u;
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
-      if (c0[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 0], (unsigned long long)(long long)c0[e]);
-      if (c1[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 1], (unsigned long long)(long long)c1[e]);
-      if (c2[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 2], (unsigned long long)(long long)c2[e]);
+      bool zn;
+      step_element<TX, TV>(a, mis, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, stepping[e], xo.e[e], vo.e[e],
+                           zn, c0[e], c1[e], c2[e]);
+      zbits |= (unsigned)zn << e;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) {
-      const int bb = i / 3, k = i - 3 * bb;
-      const unsigned long long val = s_cnt[i];
-      if (val && s_step[bb]) {
-        Counters* c = a.cnt + (int64_t)g * B + bb;
-        unsigned long long* dst = k == 0 ? &c->value : (k == 1 ? &c->a : &c->b);
-        atomicAdd(dst, val);
-      }
-    }
-    __syncthreads();
+    st_pack<TX, VEC>(Xn + base, xo);
+    st_pack<TV, VEC>(V + base, vo);
+    unsigned word = zbits << (b0 & 31);
+    for (int off = 1; off < K; off <<= 1) word |= __shfl_xor_sync(rmask, word, off);
+    if ((l % K) == 0) Zn[(int64_t)v * a.Bw + (b0 >> 5)] = word;
   }
+  flush_step_counters<VEC>(a, s_cnt, g, it, b0, c0, c1, c2, stepping);
 }
 
-template <typename TX, typename TV>
-static cudaError_t launch_tv(int vec, const StepArgs& a, int grid, cudaStream_t s) {
-  const size_t sm = (size_t)a.B * (3 * sizeof(unsigned long long) + sizeof(int));
-  switch (vec) {
-    case 1: k_step<TX, TV, 1><<<grid, 256, sm, s>>>(a); break;
-    case 2: k_step<TX, TV, 2><<<grid, 256, sm, s>>>(a); break;
-    case 4: k_step<TX, TV, 4><<<grid, 256, sm, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
+// ---------------------------------------------------------------- shared memory
+// B >= 32: one warp per row (LPR = 32), VEC = B/32 trajectories per lane, so
+// the bit words of a node are VEC words and lane l's bits lie in word
+// (l*VEC)/32.
+template <typename TX, typename TV, int VEC, bool MIS>
+__global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int it = blockIdx.x;
+  const Item item = a.g.items[it];
+  const int g = item.g;
+  const int64_t t = *a.tick;
+  if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
+  const int B = a.B;
+  constexpr int BW = VEC;  // words per node
+  const int32_t off = a.g.node_off[g];
+  const int32_t ng = a.g.node_off[g + 1] - off;
+  TX* sX = reinterpret_cast<TX*>(smem);
+  const size_t xbytes = ((size_t)ng * B * sizeof(TX) + 15) & ~(size_t)15;
+  uint32_t* sZ = reinterpret_cast<uint32_t*>(smem + xbytes);
+  const size_t zbytes = MIS ? (((size_t)ng * BW * 4 + 15) & ~(size_t)15) : 0;
+  unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem + xbytes + zbytes);
+
+  const TX* __restrict__ Xc = static_cast<const TX*>((t & 1) ? a.X1 : a.X0);
+  TX* __restrict__ Xn = static_cast<TX*>((t & 1) ? a.X0 : a.X1);
+  const uint32_t* __restrict__ Zc = (t & 1) ? a.ZX1 : a.ZX0;
+  uint32_t* __restrict__ Zn = (t & 1) ? a.ZX0 : a.ZX1;
+  TV* __restrict__ V = static_cast<TV*>(a.V);
+
+  // stage the member graph's x block (16-byte copies) and rounding words
+  {
+    const int4* src = reinterpret_cast<const int4*>(Xc + (int64_t)off * B);
+    int4* dst = reinterpret_cast<int4*>(sX);
+    const int n16 = (int)(((size_t)ng * B * sizeof(TX)) / 16);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    if (MIS) {
+      const uint32_t* zs = Zc + (int64_t)off * BW;
+      for (int i = threadIdx.x; i < ng * BW; i += blockDim.x) sZ[i] = zs[i];
+    }
+    for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int b0 = lane * VEC;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const float thr = MIS ? 0.5f : 0.0f;
+  const float lo = MIS ? 0.0f : -1.0f;
+  const bool weighted = !MIS && a.g.w != nullptr;
+  const int32_t* __restrict__ rp = a.g.row_ptr;
+  const int32_t* __restrict__ col = a.g.col;
+  const int8_t* __restrict__ wts = a.g.w;
+  constexpr int K = 32 / VEC;
+
+  bool stepping[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) stepping[e] = a.act ? (a.act[(int64_t)g * B + b0 + e] & ACT_STEP) != 0 : true;
+  int c0[VEC], c1[VEC], c2[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
+
+  for (int v = item.v0 + warp; v < item.v1; v += nwarps) {
+    const int vl = v - off;
+    const int64_t base = (int64_t)v * B + b0;
+    const Pack<TX, VEC> xv = ld_pack<TX, VEC>(sX + (int64_t)vl * B + b0);
+    const Pack<TV, VEC> vv = ld_pack_stream<TV, VEC>(V + base);
+    float acc[VEC];
+    int pos[VEC];
+    uint32_t orw[BW];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; orw[e] = 0u; }
+    const int rs = rp[v], re = rp[v + 1];
+    int wsum = 0;
+    for (int cb = rs; cb < re; cb += 32) {
+      const int j = cb + lane;
+      const int myu = j < re ? __ldcs(col + j) - off : 0;
+      const int myw = (weighted && j < re) ? (int)wts[j] : 1;
+      if (MIS && j < re) {
+#pragma unroll
+        for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu * BW + w];
+      }
+      const int cnt = min(32, re - cb);
+      int k = 0;
+      for (; k + 8 <= cnt; k += 8) {
+        int u[8], w[8];
+        Pack<TX, VEC> p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          u[q] = __shfl_sync(0xffffffffu, myu, k + q);
+          w[q] = weighted ? __shfl_sync(0xffffffffu, myw, k + q) : 1;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = ld_pack<TX, VEC>(sX + u[q] * B + b0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          wsum += w[q];
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const float f = to_f(p[q].e[e]);
+            acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
+            if (!MIS) pos[e] += (f > thr) ? w[q] : 0;
+          }
+        }
+      }
+      for (; k < cnt; ++k) {
+        const int u = __shfl_sync(0xffffffffu, myu, k);
+        const int w = weighted ? __shfl_sync(0xffffffffu, myw, k) : 1;
+        const Pack<TX, VEC> p = ld_pack<TX, VEC>(sX + u * B + b0);
+        wsum += w;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const float f = to_f(p.e[e]);
+          acc[e] = w >= 0 ? acc[e] + f : acc[e] - f;
+          if (!MIS) pos[e] += (f > thr) ? w : 0;
+        }
+      }
+    }
+    if (MIS) {
+#pragma unroll
+      for (int w = 0; w < BW; ++w) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
+      }
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) pos[e] = (orw[(b0 + e) >> 5] >> ((b0 + e) & 31)) & 1u;
+    }
+    Pack<TX, VEC> xo;
+    Pack<TV, VEC> vo;
+    unsigned zbits = 0u;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      bool zn;
+      step_element<TX, TV>(a, MIS, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, stepping[e], xo.e[e], vo.e[e],
+                           zn, c0[e], c1[e], c2[e]);
+      zbits |= (unsigned)zn << e;
+    }
+    st_pack<TX, VEC>(Xn + base, xo);
+    st_pack<TV, VEC>(V + base, vo);
+    unsigned word = zbits << (b0 & 31);
+#pragma unroll
+    for (int o = 1; o < K; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
+    if ((lane % K) == 0) Zn[(int64_t)v * BW + (b0 >> 5)] = word;
+  }
+  flush_step_counters<VEC>(a, s_cnt, g, it, b0, c0, c1, c2, stepping);
+}
+
+size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng) {
+  const size_t sx = x_dtype == DT_F32 ? 4 : 2;
+  const size_t xb = ((size_t)max_ng * B * sx + 15) & ~(size_t)15;
+  const size_t zb = problem == PROB_MIS ? (((size_t)max_ng * ((B + 31) / 32) * 4 + 15) & ~(size_t)15) : 0;
+  return xb + zb + 3 * (size_t)B * 8;
+}
+
+template <typename TX, typename TV, int VEC>
+static cudaError_t launch_vec(bool smem_path, size_t smem, bool mis, const StepArgs& a, int grid, cudaStream_t s) {
+  if (smem_path) {
+    if (mis) {
+      cudaFuncSetAttribute(k_step_s<TX, TV, VEC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_step_s<TX, TV, VEC, true><<<grid, 512, smem, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_step_s<TX, TV, VEC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_step_s<TX, TV, VEC, false><<<grid, 512, smem, s>>>(a);
+    }
+  } else {
+    k_step_g<TX, TV, VEC><<<grid, 256, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(const SolverDev& S, uint32_t* zout, Counters* cnt, const TrajState* st,
-                        const int32_t* gflag_step, int grid, cudaStream_t stream) {
+template <typename TX, typename TV>
+static cudaError_t launch_tv(int vec, bool smem_path, size_t smem, bool mis, const StepArgs& a, int grid,
+                             cudaStream_t s) {
+  switch (vec) {
+    case 1: return launch_vec<TX, TV, 1>(smem_path, smem, mis, a, grid, s);
+    case 2: return launch_vec<TX, TV, 2>(smem_path, smem, mis, a, grid, s);
+    case 4: return launch_vec<TX, TV, 4>(smem_path, smem, mis, a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, const int32_t* gflag_step,
+                        size_t smem, cudaStream_t stream) {
   StepArgs a;
   a.g = S.g;
   a.B = S.B;
   a.Bw = S.Bw;
+  a.R = S.R;
   a.problem = S.p.problem;
   a.alpha = S.p.alpha;
   a.momentum = S.p.momentum;
@@ -227,18 +423,22 @@ cudaError_t launch_step(const SolverDev& S, uint32_t* zout, Counters* cnt, const
   a.X0 = S.X0;
   a.X1 = S.X1;
   a.V = S.V;
-  a.zout = zout;
+  a.ZX0 = S.ZX0;
+  a.ZX1 = S.ZX1;
   a.cnt = cnt;
-  a.st = st;
+  a.act = act;
   a.gflag_step = gflag_step;
   a.tick = S.tick;
   const int vec = S.B >= 32 ? S.B / 32 : 1;
+  const bool sp = smem > 0;
+  const bool mis = S.p.problem == PROB_MIS;
+  const int grid = S.g.num_items;
   const int xd = S.p.x_dtype, vd = S.p.v_dtype;
-  if (xd == DT_F32) return launch_tv<float, float>(vec, a, grid, stream);
-  if (xd == DT_BF16 && vd == DT_BF16) return launch_tv<__nv_bfloat16, __nv_bfloat16>(vec, a, grid, stream);
-  if (xd == DT_BF16 && vd == DT_F32) return launch_tv<__nv_bfloat16, float>(vec, a, grid, stream);
-  if (xd == DT_F16 && vd == DT_F16) return launch_tv<__half, __half>(vec, a, grid, stream);
-  if (xd == DT_F16 && vd == DT_F32) return launch_tv<__half, float>(vec, a, grid, stream);
+  if (xd == DT_F32) return launch_tv<float, float>(vec, sp, smem, mis, a, grid, stream);
+  if (xd == DT_BF16 && vd == DT_BF16) return launch_tv<__nv_bfloat16, __nv_bfloat16>(vec, sp, smem, mis, a, grid, stream);
+  if (xd == DT_BF16 && vd == DT_F32) return launch_tv<__nv_bfloat16, float>(vec, sp, smem, mis, a, grid, stream);
+  if (xd == DT_F16 && vd == DT_F16) return launch_tv<__half, __half>(vec, sp, smem, mis, a, grid, stream);
+  if (xd == DT_F16 && vd == DT_F32) return launch_tv<__half, float>(vec, sp, smem, mis, a, grid, stream);
   return cudaErrorInvalidValue;
 }
 

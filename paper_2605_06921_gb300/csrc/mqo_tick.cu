@@ -7,6 +7,12 @@
 // the node-parallel kernels then act on (node, trajectory) pairs.  Member
 // graphs with nothing to do in a pass are skipped through per-graph tick
 // stamps written by the control kernel.
+//
+// Pair kernels map thread -> (node v, trajectory b), trajectory fastest,
+// one CTA per item (<= 256 nodes of one member graph).  The lanes that
+// share one bit word of a node (G = min(B,32) lanes) form a group; MIS set
+// logic is done on whole words: the group splits v's neighbour list, ORs
+// (or once/twice-accumulates) the neighbours' words and reduces by shuffles.
 #include "mqo_dev.cuh"
 #include "mqo_host.h"
 
@@ -41,8 +47,6 @@ __global__ void k_ctrl(CtrlArgs A) {
   const Params& p = S.p;
   const bool mis = p.problem == PROB_MIS;
   TrajState st = S.st[tau];
-  Counters c = S.cnt[tau];
-  S.cnt[tau] = Counters{0ull, 0ull, 0ull, 0ull};
   int act = 0;
   int round = RD_NONE;
 
@@ -55,7 +59,8 @@ __global__ void k_ctrl(CtrlArgs A) {
   };
 
   if (A.mode == CTRL_RESET) {
-    // forced reset (mqo_reset): round r+1 from the best set, new descent
+    // forced reset (mqo_reset): round r+1 from the best set, new descent;
+    // the counters of the last tick stay in place
     if (A.mask == nullptr || A.mask[tau]) {
       st.r += 1;
       st.s = 0;
@@ -66,7 +71,8 @@ __global__ void k_ctrl(CtrlArgs A) {
     st.act = act;
     st.round = RD_NONE;
     S.st[tau] = st;
-    S.cnt[tau] = c;  // a forced reset leaves the last counters in place
+    S.act[tau] = act;
+    S.rnd[tau] = RD_NONE;
     if (act) {
       S.gflag[g] = (int32_t)(t + 1);
       S.any[0] = (int32_t)(t + 1);
@@ -74,7 +80,9 @@ __global__ void k_ctrl(CtrlArgs A) {
     return;
   }
 
-  // fold the previous tick's exact counters
+  // fold the previous tick's exact counters (all replicas) and clear them
+  const Counters c = sum_replicas(S.cnt, tau, S.R);
+  for (int r = 0; r < S.R; ++r) S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
   const int64_t cv = (int64_t)c.value;
   st.ev_value = mis ? cv : cv / 2;
   st.ev_a = (int64_t)c.a;
@@ -191,6 +199,8 @@ __global__ void k_ctrl(CtrlArgs A) {
   st.act = act;
   st.round = round;
   S.st[tau] = st;
+  S.act[tau] = act;
+  S.rnd[tau] = round;
   const int32_t stamp = (int32_t)(t + 1);
   const int G = S.g.num_graphs;
   if (act & ACT_APPLY_MASK) {
@@ -222,72 +232,115 @@ cudaError_t launch_tick_end(const SolverDev& S, cudaStream_t stream) {
 }
 
 // ------------------------------------------------------- pair-kernel frame
-// Every pair kernel walks the items; within an item, warp w of the block
-// covers pair indices [v0*B + 32k, ...) so that each warp holds whole bit
-// words.  `body(v, b, tau, in_range)` is called by all 32 lanes together.
+struct PairCtx {
+  int g;
+  int64_t v;
+  int b;
+  int64_t tau;
+  bool in;
+  int gl;          // lane within the word group
+  int G;           // group size min(B, 32)
+  unsigned gmask;  // lanes of the group
+  int wk;          // word index of the group inside the node
+};
+
+// Walk the (node, trajectory) pairs of one item; warp w covers pair
+// indices [v0*B + 32k, ...) so that each group holds one whole bit word.
+// `body(ctx)` is called by all 32 lanes together.
 template <typename Body>
-__device__ __forceinline__ void for_pairs(const SolverDev& S, const int32_t* gstamp, int64_t stamp, Body body) {
+__device__ __forceinline__ void item_pairs(const SolverDev& S, const Item& item, Body body) {
   const int B = S.B;
   const int lane = threadIdx.x & 31;
-  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
-    const Item item = S.g.items[it];
-    if (gstamp && gstamp[item.g] != (int32_t)stamp) continue;
-    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
-    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
-      const int64_t idx = base + lane;
-      const bool in = idx < hi;
-      const int64_t v = in ? idx / B : (int64_t)item.v0;
-      const int b = (int)(idx % B);
-      body(item.g, v, b, (int64_t)item.g * B + b, in);
-    }
+  const int G = B < 32 ? B : 32;
+  const int gbase = lane & ~(G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+  const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
+  for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+    const int64_t idx = base + lane;
+    PairCtx c;
+    c.in = idx < hi;
+    c.v = c.in ? idx / B : (int64_t)item.v0;
+    c.b = (int)(idx % B);
+    c.g = item.g;
+    c.tau = (int64_t)item.g * B + c.b;
+    c.gl = lane - gbase;
+    c.G = G;
+    c.gmask = gmask;
+    c.wk = c.b >> 5;
+    body(c);
   }
+}
+
+// OR over the neighbours u of v (only u < v if `less`) of word wk, computed
+// by the lanes of a group together.
+__device__ __forceinline__ uint32_t group_nb_or(const SolverDev& S, const uint32_t* words, const PairCtx& c,
+                                                bool less) {
+  const int32_t* rp = S.g.row_ptr;
+  const int32_t* col = S.g.col;
+  uint32_t r = 0u;
+  for (int32_t j = rp[c.v] + c.gl; j < rp[c.v + 1]; j += c.G) {
+    const int32_t u = col[j];
+    if (less && u >= c.v) break;  // rows are sorted ascending
+    r |= words[(int64_t)u * S.Bw + c.wk];
+  }
+  for (int o = 1; o < c.G; o <<= 1) r |= __shfl_xor_sync(c.gmask, r, o);
+  return r;
 }
 
 // ---------------------------------------------------------------- apply
 __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
+  const int it = blockIdx.x;
   const int64_t t = *S.tick;
   if (S.any[0] != (int32_t)(t + 1)) return;
+  const Item item = S.g.items[it];
+  if (S.gflag[item.g] != (int32_t)(t + 1)) return;
   const int B = S.B, Bw = S.Bw;
   const bool mis = S.p.problem == PROB_MIS;
+  const float thr = mis ? 0.5f : 0.0f;
   void* Xc = (t & 1) ? S.X1 : S.X0;
-  for_pairs(S, S.gflag, t + 1, [&](int g, int64_t v, int b, int64_t tau, bool in) {
-    const int act = in ? S.st[tau].act : 0;
+  uint32_t* Zc = (t & 1) ? S.ZX1 : S.ZX0;
+  const uint32_t* Zp = (t & 1) ? S.ZX0 : S.ZX1;  // rounding of the x the last step evaluated
+  item_pairs(S, item, [&](const PairCtx& c) {
+    const int64_t v = c.v;
+    const int b = c.b;
+    const int act = c.in ? S.act[c.tau] : 0;
     const bool acc_zx = act & ACT_ACC_ZX, acc_w = act & ACT_ACC_WORK;
     bool zb = false;
-    if (in) zb = get_bit(S.Zbest, v, Bw, b);
+    if (c.in) zb = get_bit(S.Zbest, v, Bw, b);
     bool src = false;
-    if (acc_zx) src = get_bit(S.ZXP, v, Bw, b);
+    if (acc_zx) src = get_bit(Zp, v, Bw, b);
     if (acc_w) src = get_bit(S.Zwork, v, Bw, b);
     const bool acc = acc_zx || acc_w;
     if (acc) zb = src;
     update_word(S.Zbest, v, Bw, b, B, src, acc);
     bool wv = false;
-    if (act & ACT_WORK_ZX) wv = get_bit(S.ZXP, v, Bw, b);
+    if (act & ACT_WORK_ZX) wv = get_bit(Zp, v, Bw, b);
     if (act & ACT_WORK_BEST) wv = zb;
     update_word(S.Zwork, v, Bw, b, B, wv, (act & (ACT_WORK_ZX | ACT_WORK_BEST)) != 0);
-    if (act & (ACT_RESET | ACT_INIT)) {
-      const int32_t off = S.g.node_off[g];
+    const bool newx = (act & (ACT_RESET | ACT_INIT)) != 0;
+    float x = 0.0f;
+    if (newx) {
+      const int32_t off = S.g.node_off[c.g];
       const uint32_t vl = (uint32_t)(v - off);
-      float x;
       if (act & ACT_RESET) {
-        const TrajState& st = S.st[tau];
+        const TrajState& st = S.st[c.tau];
         x = zb ? 1.0f : (mis ? 0.0f : -1.0f);
-        const uint32_t n_g = (uint32_t)(S.g.node_off[g + 1] - off);
+        const uint32_t n_g = (uint32_t)(S.g.node_off[c.g + 1] - off);
         uint32_t keys[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) keys[i] = st.rkeys[i];
         if ((int64_t)feistel_sigma(n_g, keys, vl) < st.rk) x = 0.0f;
       } else {
         const Params& p = S.p;
-        const int32_t o = S.st[tau].o;
-        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)o, (uint64_t)vl, 0ULL, p.seed, (uint64_t)tau);
+        const int32_t o = S.st[c.tau].o;
+        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)o, (uint64_t)vl, 0ULL, p.seed, (uint64_t)c.tau);
         const float lo = mis ? 0.0f : -1.0f, hi = 1.0f;
         if (p.init_kind == 0) {
           const float u = unit24(r.v[0]);
           x = lo + (hi - lo) * u;
         } else {
           const int32_t d = S.g.row_ptr[v + 1] - S.g.row_ptr[v];
-          const int32_t dm = S.g.dmax[g];
+          const int32_t dm = S.g.dmax[c.g];
           const float q = dm > 0 ? (float)d / (float)dm : 0.0f;
           float base = 1.0f - q;
           if (!mis) base = 2.0f * base - 1.0f;
@@ -301,235 +354,235 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
         }
       }
       const int64_t e = v * B + b;
-      if (S.p.x_dtype == DT_F32) static_cast<float*>(Xc)[e] = x;
-      else if (S.p.x_dtype == DT_BF16) static_cast<__nv_bfloat16*>(Xc)[e] = __float2bfloat16_rn(x);
-      else static_cast<__half*>(Xc)[e] = __float2half_rn(x);
+      if (S.p.x_dtype == DT_F32) {
+        static_cast<float*>(Xc)[e] = x;
+      } else if (S.p.x_dtype == DT_BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        static_cast<__nv_bfloat16*>(Xc)[e] = h;
+        x = __bfloat162float(h);
+      } else {
+        const __half h = __float2half_rn(x);
+        static_cast<__half*>(Xc)[e] = h;
+        x = __half2float(h);
+      }
       if (S.p.v_dtype == DT_F32) static_cast<float*>(S.V)[e] = 0.0f;
       else if (S.p.v_dtype == DT_BF16) static_cast<__nv_bfloat16*>(S.V)[e] = __float2bfloat16_rn(0.0f);
       else static_cast<__half*>(S.V)[e] = __float2half_rn(0.0f);
     }
+    update_word(Zc, v, Bw, b, B, x > thr, newx);
   });
 }
 
-cudaError_t launch_apply(const SolverDev& S, int grid, cudaStream_t stream) {
-  k_apply<<<grid, kPairThreads, 0, stream>>>(S);
+cudaError_t launch_apply(const SolverDev& S, cudaStream_t stream) {
+  k_apply<<<S.g.num_items, kPairThreads, 0, stream>>>(S);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- discrete rounds
-// Block-level counter reduction for pair kernels: per item, per trajectory.
-struct CntAcc {
-  long long v0, v1, v2, v3;
-};
-
-__device__ __forceinline__ void flush_counters(const SolverDev& S, unsigned long long* s_cnt, int g, int B,
-                                               Counters* dst) {
+__device__ __forceinline__ void flush_pair_counters(const SolverDev& S, unsigned long long* s_cnt, int g, int it,
+                                                    Counters* dst) {
   __syncthreads();
+  const int B = S.B;
+  const int rep = it % S.R;
   for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) {
     const unsigned long long val = s_cnt[i];
     if (val) {
-      Counters* c = dst + (int64_t)g * B + i / 4;
+      Counters* c = dst + ((int64_t)g * B + i / 4) * S.R + rep;
       const int k = i & 3;
       unsigned long long* p = k == 0 ? &c->value : k == 1 ? &c->a : k == 2 ? &c->b : &c->commits;
       atomicAdd(p, val);
     }
-    s_cnt[i] = 0ull;
   }
-  __syncthreads();
 }
 
 // pass 0 = A (decide / propose), 1 = B (commit), 2 = C (count)
 __global__ void __launch_bounds__(kPairThreads) k_disc(SolverDev S, int pass) {
   __shared__ unsigned long long s_cnt[4 * 128];
+  const int it = blockIdx.x;
   const int64_t t = *S.tick;
   if (S.any[1] != (int32_t)(t + 1)) return;
+  const Item item = S.g.items[it];
+  const int G = S.g.num_graphs;
+  if (S.gflag[G + item.g] != (int32_t)(t + 1)) return;
   const int B = S.B, Bw = S.Bw;
   const bool mis = S.p.problem == PROB_MIS;
-  const int G = S.g.num_graphs;
   const int32_t* rp = S.g.row_ptr;
   const int32_t* col = S.g.col;
   const int8_t* wts = S.g.w;
   for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) s_cnt[i] = 0ull;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
-    const Item item = S.g.items[it];
-    if (S.gflag[G + item.g] != (int32_t)(t + 1)) continue;
-    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
-    long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-    int my_b = -1;
-    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
-      const int64_t idx = base + lane;
-      const bool in = idx < hi;
-      const int64_t v = in ? idx / B : (int64_t)item.v0;
-      const int b = (int)(idx % B);
-      const int64_t tau = (int64_t)item.g * B + b;
-      const int round = in ? S.st[tau].round : RD_NONE;
-      my_b = b;
-      const int64_t e = v * B + b;
-      const int32_t rs = rp[v], re = rp[v + 1];
-      if (pass == 0) {
-        // ---------------- pass A
-        bool dropv = false;
-        if (round == RD_DROP && get_bit(S.Zwork, v, Bw, b)) {
-          for (int32_t j = rs; j < re; ++j) {
-            const int32_t u = col[j];
-            if (u < v && get_bit(S.Zwork, u, Bw, b)) { dropv = true; break; }
-          }
-        }
-        update_word(S.Zdrop, v, Bw, b, B, dropv, round == RD_DROP);
-        acc3 += dropv;
-        bool addv = false;
-        if (round == RD_COMPLETE && get_bit(S.Zfree, v, Bw, b)) {
-          addv = true;
-          for (int32_t j = rs; j < re; ++j) {
-            const int32_t u = col[j];
-            if (u < v && get_bit(S.Zfree, u, Bw, b)) { addv = false; break; }
-          }
-        }
-        bool flipv = false;
-        if (round == RD_FLIP1 && get_bit(S.Zaux, v, Bw, b)) {
-          flipv = true;
-          for (int32_t j = rs; j < re; ++j) {
-            const int32_t u = col[j];
-            if (u < v && get_bit(S.Zaux, u, Bw, b)) { flipv = false; break; }
-          }
-        }
-        const bool zv = get_bit(S.Zwork, v, Bw, b);
-        // complete sets bits, flip1 toggles: both are own-word updates
-        update_word(S.Zwork, v, Bw, b, B, addv ? true : !zv, addv || flipv);
-        acc3 += addv + flipv;
-        if (round == RD_SWAP) {
-          int32_t fa = -1, fb = -1;
-          if (zv) {
-            for (int32_t i = rs; i < re && fa < 0; ++i) {
-              const int32_t a = col[i];
-              if (!get_bit(S.Zaux, a, Bw, b)) continue;
-              for (int32_t j = i + 1; j < re; ++j) {
-                const int32_t c = col[j];
-                if (!get_bit(S.Zaux, c, Bw, b)) continue;
-                if (!sorted_contains(col, rp[a], rp[a + 1], c)) { fa = a; fb = c; break; }
-              }
-            }
-          }
-          S.pa[e] = fa;
-          S.pb[e] = fb;
-          if (fa >= 0) {
-            S.owner[(int64_t)fa * B + b] = (int32_t)v;
-            S.owner[(int64_t)fb * B + b] = (int32_t)v;
-          }
-        }
-        if (round == RD_FLIP2) {
-          int32_t fb = -1;
-          const int32_t ga = S.gain[e];
-          for (int32_t j = rs; j < re; ++j) {
-            const int32_t u = col[j];
-            if (u <= v) continue;
-            if (get_bit(S.Zwork, u, Bw, b) == zv) continue;
-            const int w = wts ? (int)wts[j] : 1;
-            if (ga + S.gain[(int64_t)u * B + b] + 2 * w > 0) { fb = u; break; }
-          }
-          S.pb[e] = fb;
-          if (fb >= 0) {
-            atomicMin(&S.owner[e], (int32_t)v);
-            atomicMin(&S.owner[(int64_t)fb * B + b], (int32_t)v);
-          }
-        }
-      } else if (pass == 1) {
-        // ---------------- pass B
-        const bool dv = round == RD_DROP && get_bit(S.Zdrop, v, Bw, b);
-        update_word_atomic(S.Zwork, v, Bw, b, B, false, dv);
-        if (round == RD_SWAP) {
-          const int32_t fa = S.pa[e];
-          if (fa >= 0) {
-            const int32_t fb = S.pb[e];
-            bool ok = true;
-            const int32_t ends[2] = {fa, fb};
-            for (int k = 0; k < 2 && ok; ++k) {
-              const int32_t x = ends[k];
-              for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
-                const int32_t o = S.owner[(int64_t)col[j] * B + b];
-                if (o < (int32_t)v) { ok = false; break; }
-              }
-            }
-            if (ok) {
-              const uint32_t bit = 1u << (b & 31);
-              atomicAnd(&S.Zwork[v * Bw + (b >> 5)], ~bit);
-              atomicOr(&S.Zwork[(int64_t)fa * Bw + (b >> 5)], bit);
-              atomicOr(&S.Zwork[(int64_t)fb * Bw + (b >> 5)], bit);
-              acc3 += 1;
-            }
-          }
-        }
-        if (round == RD_FLIP2) {
-          const int32_t fb = S.pb[e];
-          if (fb >= 0) {
-            bool ok = S.owner[e] == (int32_t)v && S.owner[(int64_t)fb * B + b] == (int32_t)v;
-            const int32_t ends[2] = {(int32_t)v, fb};
-            for (int k = 0; k < 2 && ok; ++k) {
-              const int32_t x = ends[k];
-              for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
-                const int32_t y = col[j];
-                if (y == (int32_t)v || y == fb) continue;
-                if (S.owner[(int64_t)y * B + b] < (int32_t)v) { ok = false; break; }
-              }
-            }
-            if (ok) {
-              const uint32_t bit = 1u << (b & 31);
-              atomicXor(&S.Zwork[v * Bw + (b >> 5)], bit);
-              atomicXor(&S.Zwork[(int64_t)fb * Bw + (b >> 5)], bit);
-              acc3 += 1;
-            }
-          }
-        }
-      } else {
-        // ---------------- pass C: counts of the (new) work set
-        const bool act = round != RD_NONE;
-        const bool zv = get_bit(S.Zwork, v, Bw, b);
-        bool aux = false, fr = false;
-        if (act) {
-          S.owner[e] = 0x7fffffff;
-          if (mis) {
-            int c = 0;
-            for (int32_t j = rs; j < re && c < 2; ++j) c += get_bit(S.Zwork, col[j], Bw, b);
-            acc0 += zv;
-            acc1 += zv && c > 0;
-            fr = !zv && c == 0;
-            acc2 += fr;
-            aux = !zv && c == 1;  // tight
-          } else {
-            int P = 0, W = 0;
-            for (int32_t j = rs; j < re; ++j) {
-              const int w = wts ? (int)wts[j] : 1;
-              W += w;
-              if (get_bit(S.Zwork, col[j], Bw, b)) P += w;
-            }
-            const int as = 2 * P - W;
-            acc0 += zv ? (W - P) : P;
-            const bool fixed = zv ? (as <= -1) : (as >= 0);
-            acc1 += !fixed;
-            const int gn = zv ? as : -as;
-            acc2 += gn > 0;
-            S.gain[e] = gn;
-            aux = gn > 0;
-          }
-        }
-        update_word(S.Zaux, v, Bw, b, B, aux, act);
-        update_word(S.Zfree, v, Bw, b, B, fr, act && mis);
+  long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+  int my_b = (int)(threadIdx.x % B);
+  item_pairs(S, item, [&](const PairCtx& c) {
+    const int64_t v = c.v;
+    const int b = c.b;
+    const int round = c.in ? S.rnd[c.tau] : RD_NONE;
+    const int64_t e = v * B + b;
+    const int32_t rs = rp[v], re = rp[v + 1];
+    const uint32_t bit = 1u << (b & 31);
+    if (pass == 0) {
+      // ---------------- pass A
+      const bool zv = get_bit(S.Zwork, v, Bw, b);
+      const bool need_drop = __any_sync(c.gmask, round == RD_DROP);
+      const bool need_comp = __any_sync(c.gmask, round == RD_COMPLETE);
+      const bool need_flip = __any_sync(c.gmask, round == RD_FLIP1);
+      bool dropv = false, addv = false, flipv = false;
+      if (need_drop) {
+        const uint32_t o = group_nb_or(S, S.Zwork, c, true);
+        dropv = round == RD_DROP && zv && (o & bit);
       }
+      if (need_comp) {
+        const uint32_t o = group_nb_or(S, S.Zfree, c, true);
+        addv = round == RD_COMPLETE && get_bit(S.Zfree, v, Bw, b) && !(o & bit);
+      }
+      if (need_flip) {
+        const uint32_t o = group_nb_or(S, S.Zaux, c, true);
+        flipv = round == RD_FLIP1 && get_bit(S.Zaux, v, Bw, b) && !(o & bit);
+      }
+      update_word(S.Zdrop, v, Bw, b, B, dropv, round == RD_DROP);
+      // complete sets bits, flip1 toggles: both are own-word updates
+      update_word(S.Zwork, v, Bw, b, B, addv ? true : !zv, addv || flipv);
+      acc3 += dropv + addv + flipv;
+      if (round == RD_SWAP) {
+        int32_t fa = -1, fb = -1;
+        if (zv) {
+          for (int32_t i = rs; i < re && fa < 0; ++i) {
+            const int32_t a = col[i];
+            if (!get_bit(S.Zaux, a, Bw, b)) continue;
+            for (int32_t j = i + 1; j < re; ++j) {
+              const int32_t cc = col[j];
+              if (!get_bit(S.Zaux, cc, Bw, b)) continue;
+              if (!sorted_contains(col, rp[a], rp[a + 1], cc)) { fa = a; fb = cc; break; }
+            }
+          }
+        }
+        S.pa[e] = fa;
+        S.pb[e] = fb;
+        if (fa >= 0) {
+          S.owner[(int64_t)fa * B + b] = (int32_t)v;
+          S.owner[(int64_t)fb * B + b] = (int32_t)v;
+        }
+      }
+      if (round == RD_FLIP2) {
+        int32_t fb = -1;
+        const int32_t ga = S.gain[e];
+        for (int32_t j = rs; j < re; ++j) {
+          const int32_t u = col[j];
+          if (u <= v) continue;
+          if (get_bit(S.Zwork, u, Bw, b) == zv) continue;
+          const int w = wts ? (int)wts[j] : 1;
+          if (ga + S.gain[(int64_t)u * B + b] + 2 * w > 0) { fb = u; break; }
+        }
+        S.pb[e] = fb;
+        if (fb >= 0) {
+          atomicMin(&S.owner[e], (int32_t)v);
+          atomicMin(&S.owner[(int64_t)fb * B + b], (int32_t)v);
+        }
+      }
+    } else if (pass == 1) {
+      // ---------------- pass B
+      const bool dv = round == RD_DROP && get_bit(S.Zdrop, v, Bw, b);
+      update_word_atomic(S.Zwork, v, Bw, b, B, false, dv);
+      if (round == RD_SWAP) {
+        const int32_t fa = S.pa[e];
+        if (fa >= 0) {
+          const int32_t fb = S.pb[e];
+          bool ok = true;
+          const int32_t ends[2] = {fa, fb};
+          for (int k = 0; k < 2 && ok; ++k) {
+            const int32_t x = ends[k];
+            for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+              const int32_t o = S.owner[(int64_t)col[j] * B + b];
+              if (o < (int32_t)v) { ok = false; break; }
+            }
+          }
+          if (ok) {
+            atomicAnd(&S.Zwork[v * Bw + (b >> 5)], ~bit);
+            atomicOr(&S.Zwork[(int64_t)fa * Bw + (b >> 5)], bit);
+            atomicOr(&S.Zwork[(int64_t)fb * Bw + (b >> 5)], bit);
+            acc3 += 1;
+          }
+        }
+      }
+      if (round == RD_FLIP2) {
+        const int32_t fb = S.pb[e];
+        if (fb >= 0) {
+          bool ok = S.owner[e] == (int32_t)v && S.owner[(int64_t)fb * B + b] == (int32_t)v;
+          const int32_t ends[2] = {(int32_t)v, fb};
+          for (int k = 0; k < 2 && ok; ++k) {
+            const int32_t x = ends[k];
+            for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+              const int32_t y = col[j];
+              if (y == (int32_t)v || y == fb) continue;
+              if (S.owner[(int64_t)y * B + b] < (int32_t)v) { ok = false; break; }
+            }
+          }
+          if (ok) {
+            atomicXor(&S.Zwork[v * Bw + (b >> 5)], bit);
+            atomicXor(&S.Zwork[(int64_t)fb * Bw + (b >> 5)], bit);
+            acc3 += 1;
+          }
+        }
+      }
+    } else {
+      // ---------------- pass C: counts of the (new) work set
+      const bool act = round != RD_NONE;
+      const bool zv = get_bit(S.Zwork, v, Bw, b);
+      bool aux = false, fr = false;
+      if (act) S.owner[e] = 0x7fffffff;
+      if (mis) {
+        if (__any_sync(c.gmask, act)) {
+          // once / twice: neighbours with the bit set at least once / twice
+          uint32_t once = 0u, twice = 0u;
+          for (int32_t j = rs + c.gl; j < re; j += c.G) {
+            const uint32_t w = S.Zwork[(int64_t)col[j] * Bw + c.wk];
+            twice |= once & w;
+            once |= w;
+          }
+          for (int o = 1; o < c.G; o <<= 1) {
+            const uint32_t o2 = __shfl_xor_sync(c.gmask, once, o);
+            const uint32_t t2 = __shfl_xor_sync(c.gmask, twice, o);
+            twice = twice | t2 | (once & o2);
+            once |= o2;
+          }
+          if (act) {
+            const bool one = (once & bit) != 0, two = (twice & bit) != 0;
+            acc0 += zv;
+            acc1 += zv && one;
+            fr = !zv && !one;
+            acc2 += fr;
+            aux = !zv && one && !two;  // tight: exactly one neighbour in the set
+          }
+        }
+      } else if (act) {
+        int P = 0, W = 0;
+        for (int32_t j = rs; j < re; ++j) {
+          const int w = wts ? (int)wts[j] : 1;
+          W += w;
+          if (get_bit(S.Zwork, col[j], Bw, b)) P += w;
+        }
+        const int as = 2 * P - W;
+        acc0 += zv ? (W - P) : P;
+        const bool fixed = zv ? (as <= -1) : (as >= 0);
+        acc1 += !fixed;
+        const int gn = zv ? as : -as;
+        acc2 += gn > 0;
+        S.gain[e] = gn;
+        aux = gn > 0;
+      }
+      update_word(S.Zaux, v, Bw, b, B, aux, act);
+      update_word(S.Zfree, v, Bw, b, B, fr, act && mis);
     }
-    if (my_b >= 0) {
-      if (acc0) atomicAdd(&s_cnt[4 * my_b + 0], (unsigned long long)acc0);
-      if (acc1) atomicAdd(&s_cnt[4 * my_b + 1], (unsigned long long)acc1);
-      if (acc2) atomicAdd(&s_cnt[4 * my_b + 2], (unsigned long long)acc2);
-      if (acc3) atomicAdd(&s_cnt[4 * my_b + 3], (unsigned long long)acc3);
-    }
-    flush_counters(S, s_cnt, item.g, B, S.cnt);
-  }
+  });
+  if (acc0) atomicAdd(&s_cnt[4 * my_b + 0], (unsigned long long)acc0);
+  if (acc1) atomicAdd(&s_cnt[4 * my_b + 1], (unsigned long long)acc1);
+  if (acc2) atomicAdd(&s_cnt[4 * my_b + 2], (unsigned long long)acc2);
+  if (acc3) atomicAdd(&s_cnt[4 * my_b + 3], (unsigned long long)acc3);
+  flush_pair_counters(S, s_cnt, item.g, it, S.cnt);
 }
 
-cudaError_t launch_disc(const SolverDev& S, int pass, int grid, cudaStream_t stream) {
-  k_disc<<<grid, kPairThreads, 0, stream>>>(S, pass);
+cudaError_t launch_disc(const SolverDev& S, int pass, cudaStream_t stream) {
+  k_disc<<<S.g.num_items, kPairThreads, 0, stream>>>(S, pass);
   return cudaGetLastError();
 }
 
@@ -539,20 +592,21 @@ __global__ void __launch_bounds__(kPairThreads) k_round_bits(SolverDev S, uint32
   const void* Xc = (t & 1) ? S.X1 : S.X0;
   const bool mis = S.p.problem == PROB_MIS;
   const float thr = mis ? 0.5f : 0.0f;
-  for_pairs(S, nullptr, 0, [&](int g, int64_t v, int b, int64_t tau, bool in) {
+  const Item item = S.g.items[blockIdx.x];
+  item_pairs(S, item, [&](const PairCtx& c) {
     float x = 0.0f;
-    if (in) {
-      const int64_t e = v * S.B + b;
+    if (c.in) {
+      const int64_t e = c.v * S.B + c.b;
       if (S.p.x_dtype == DT_F32) x = static_cast<const float*>(Xc)[e];
       else if (S.p.x_dtype == DT_BF16) x = __bfloat162float(static_cast<const __nv_bfloat16*>(Xc)[e]);
       else x = __half2float(static_cast<const __half*>(Xc)[e]);
     }
-    update_word(z, v, S.Bw, b, S.B, x > thr, in);
+    update_word(z, c.v, S.Bw, c.b, S.B, x > thr, c.in);
   });
 }
 
-cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, int grid, cudaStream_t stream) {
-  k_round_bits<<<grid, kPairThreads, 0, stream>>>(S, z);
+cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, cudaStream_t stream) {
+  k_round_bits<<<S.g.num_items, kPairThreads, 0, stream>>>(S, z);
   return cudaGetLastError();
 }
 
@@ -565,60 +619,55 @@ __global__ void __launch_bounds__(kPairThreads) k_eval(SolverDev S, const uint32
   const int32_t* rp = S.g.row_ptr;
   const int32_t* col = S.g.col;
   const int8_t* wts = S.g.w;
+  const int it = blockIdx.x;
+  const Item item = S.g.items[it];
   for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) s_cnt[i] = 0ull;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
-    const Item item = S.g.items[it];
-    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
-    long long a0 = 0, a1 = 0, a2 = 0;
-    int my_b = -1;
-    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
-      const int64_t idx = base + lane;
-      if (idx >= hi) continue;
-      const int64_t v = idx / B;
-      const int b = (int)(idx % B);
-      my_b = b;
-      const bool zv = get_bit(z, v, Bw, b);
-      if (mis) {
-        int c = 0;
-        for (int32_t j = rp[v]; j < rp[v + 1]; ++j) c += get_bit(z, col[j], Bw, b);
-        a0 += zv;
-        a1 += zv ? c : 0;
-        a2 += !zv && c == 0;
-      } else {
-        int P = 0, W = 0;
-        for (int32_t j = rp[v]; j < rp[v + 1]; ++j) {
-          const int w = wts ? (int)wts[j] : 1;
-          W += w;
-          if (get_bit(z, col[j], Bw, b)) P += w;
-        }
-        const int as = 2 * P - W;
-        a0 += zv ? (W - P) : P;
-        a1 += !(zv ? (as <= -1) : (as >= 0));
-        a2 += (zv ? as : -as) > 0;
+  long long a0 = 0, a1 = 0, a2 = 0;
+  const int my_b = (int)(threadIdx.x % B);
+  item_pairs(S, item, [&](const PairCtx& c) {
+    if (!c.in) return;
+    const int64_t v = c.v;
+    const int b = c.b;
+    const bool zv = get_bit(z, v, Bw, b);
+    if (mis) {
+      int cnt = 0;
+      for (int32_t j = rp[v]; j < rp[v + 1]; ++j) cnt += get_bit(z, col[j], Bw, b);
+      a0 += zv;
+      a1 += zv ? cnt : 0;
+      a2 += !zv && cnt == 0;
+    } else {
+      int P = 0, W = 0;
+      for (int32_t j = rp[v]; j < rp[v + 1]; ++j) {
+        const int w = wts ? (int)wts[j] : 1;
+        W += w;
+        if (get_bit(z, col[j], Bw, b)) P += w;
       }
+      const int as = 2 * P - W;
+      a0 += zv ? (W - P) : P;
+      a1 += !(zv ? (as <= -1) : (as >= 0));
+      a2 += (zv ? as : -as) > 0;
     }
-    if (my_b >= 0) {
-      if (a0) atomicAdd(&s_cnt[4 * my_b + 0], (unsigned long long)a0);
-      if (a1) atomicAdd(&s_cnt[4 * my_b + 1], (unsigned long long)a1);
-      if (a2) atomicAdd(&s_cnt[4 * my_b + 2], (unsigned long long)a2);
-    }
-    flush_counters(S, s_cnt, item.g, B, out);
-  }
+  });
+  if (a0) atomicAdd(&s_cnt[4 * my_b + 0], (unsigned long long)a0);
+  if (a1) atomicAdd(&s_cnt[4 * my_b + 1], (unsigned long long)a1);
+  if (a2) atomicAdd(&s_cnt[4 * my_b + 2], (unsigned long long)a2);
+  flush_pair_counters(S, s_cnt, item.g, it, out);
 }
 
-cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, int grid, cudaStream_t stream) {
-  k_eval<<<grid, kPairThreads, 0, stream>>>(S, z, out);
+cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, cudaStream_t stream) {
+  k_eval<<<S.g.num_items, kPairThreads, 0, stream>>>(S, z, out);
   return cudaGetLastError();
 }
 
-// counters -> user arrays. kind 0: step/machine counters (MaxCut value is 2*cut);
-// kind 1: evaluation counters (MIS a = 2*edges, MaxCut value = 2*cut)
-__global__ void k_counters_out(Counters* c, int64_t T, int mis, int kind, int64_t* value, int64_t* a, int64_t* b) {
+// counters (R replicas) -> user arrays. kind 0: step/machine counters
+// (MaxCut value is 2*cut); kind 1: evaluation counters (MIS a = 2*edges,
+// MaxCut value = 2*cut)
+__global__ void k_counters_out(const Counters* c, int64_t T, int R, int mis, int kind, int64_t* value, int64_t* a,
+                               int64_t* b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= T) return;
-  const Counters x = c[i];
+  const Counters x = sum_replicas(c, i, R);
   int64_t v = (int64_t)x.value, aa = (int64_t)x.a;
   if (!mis) v /= 2;
   if (mis && kind == 1) aa /= 2;
@@ -630,8 +679,8 @@ __global__ void k_counters_out(Counters* c, int64_t T, int mis, int kind, int64_
 cudaError_t launch_counters_out(const SolverDev& S, const Counters* c, int64_t* value, int64_t* a, int64_t* b,
                                 int kind, cudaStream_t stream) {
   const int64_t T = (int64_t)S.g.num_graphs * S.B;
-  k_counters_out<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(const_cast<Counters*>(c), T,
-                                                                  S.p.problem == PROB_MIS, kind, value, a, b);
+  k_counters_out<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(c, T, S.R, S.p.problem == PROB_MIS, kind, value,
+                                                                  a, b);
   return cudaGetLastError();
 }
 
@@ -651,38 +700,27 @@ __global__ void __launch_bounds__(kPairThreads) k_objective(SolverDev S, double*
   };
   for (int i = threadIdx.x; i < B; i += blockDim.x) s_obj[i] = 0.0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (int it = blockIdx.x; it < S.g.num_items; it += gridDim.x) {
-    const Item item = S.g.items[it];
-    const int64_t lo = (int64_t)item.v0 * B, hi = (int64_t)item.v1 * B;
-    double part = 0.0;
-    for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
-      const int64_t idx = base + lane;
-      if (idx >= hi) continue;
-      const int64_t v = idx / B;
-      const int b = (int)(idx % B);
-      float acc = 0.0f;
-      for (int32_t j = S.g.row_ptr[v]; j < S.g.row_ptr[v + 1]; ++j) {
-        const float xu = ld((int64_t)S.g.col[j] * B + b);
-        if (S.g.w == nullptr || S.g.w[j] >= 0) acc = acc + xu;
-        else acc = acc - xu;
-      }
-      const double xv = (double)ld(v * B + b);
-      part += mis ? xv - 0.5 * (double)S.p.gamma * xv * (double)acc
-                  : -(double)S.p.lambda_ * xv - xv * (double)acc;
+  const Item item = S.g.items[blockIdx.x];
+  double part = 0.0;
+  item_pairs(S, item, [&](const PairCtx& c) {
+    if (!c.in) return;
+    float acc = 0.0f;
+    for (int32_t j = S.g.row_ptr[c.v]; j < S.g.row_ptr[c.v + 1]; ++j) {
+      const float xu = ld((int64_t)S.g.col[j] * B + c.b);
+      if (S.g.w == nullptr || S.g.w[j] >= 0) acc = acc + xu;
+      else acc = acc - xu;
     }
-    if (part != 0.0) atomicAdd(&s_obj[threadIdx.x % B], part);
-    __syncthreads();
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-      if (s_obj[i] != 0.0) atomicAdd(&out[(int64_t)item.g * B + i], s_obj[i]);
-      s_obj[i] = 0.0;
-    }
-    __syncthreads();
-  }
+    const double xv = (double)ld(c.v * B + c.b);
+    part += mis ? xv - 0.5 * (double)S.p.gamma * xv * (double)acc : -(double)S.p.lambda_ * xv - xv * (double)acc;
+  });
+  if (part != 0.0) atomicAdd(&s_obj[threadIdx.x % B], part);
+  __syncthreads();
+  for (int i = threadIdx.x; i < B; i += blockDim.x)
+    if (s_obj[i] != 0.0) atomicAdd(&out[(int64_t)item.g * B + i], s_obj[i]);
 }
 
-cudaError_t launch_objective(const SolverDev& S, double* out, int grid, cudaStream_t stream) {
-  k_objective<<<grid, kPairThreads, 0, stream>>>(S, out);
+cudaError_t launch_objective(const SolverDev& S, double* out, cudaStream_t stream) {
+  k_objective<<<S.g.num_items, kPairThreads, 0, stream>>>(S, out);
   return cudaGetLastError();
 }
 
@@ -701,10 +739,6 @@ cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStre
   k_ls_merge<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(S.st, saved, T);
   return cudaGetLastError();
 }
-
-}  // namespace mqo
-
-namespace mqo {
 
 // fresh machine state for every trajectory: first descent of outer
 // iteration 0, no best set; the apply pass then writes the initial x
@@ -730,7 +764,9 @@ __global__ void k_state_init(SolverDev S) {
     for (int i = 0; i < 6; ++i) st.rkeys[i] = 0u;
     st.rk = 0;
     S.st[tau] = st;
-    S.cnt[tau] = Counters{0ull, 0ull, 0ull, 0ull};
+    S.act[tau] = ACT_INIT;
+    S.rnd[tau] = RD_NONE;
+    for (int r = 0; r < S.R; ++r) S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
     const int g = (int)(tau / S.B);
     S.gflag[g] = (int32_t)(t + 1);
   }

@@ -129,6 +129,18 @@ def test_plain_steps_batch_sizes_mis(mq, B):
     _plain_steps(mq, small_batch(3, seed=B), mq.params(batch=B, alpha=0.8, momentum=0.45, seed=B), 12)
 
 
+@pytest.mark.parametrize("problem", [0, 1])
+@pytest.mark.parametrize("B,xd", [(32, 0), (32, 1), (64, 0), (128, 1)])
+def test_generic_step_kernel_on_small_graphs(mq, monkeypatch, problem, B, xd):
+    """the global-memory step kernel (used for large graphs) on graphs that
+    would otherwise take the shared-memory kernel"""
+    monkeypatch.setenv("MQO_STEP_KERNEL", "generic")
+    p = mq.params(problem=problem, batch=B, x_dtype=xd, alpha=0.8 if problem == 0 else 0.05, momentum=0.5, seed=B)
+    _plain_steps(mq, small_batch(2, seed=B + 1), p, 8)
+    G = small_batch(2, 30, 60, 0.15, seed=B)
+    _machine(mq, G, mq.params(problem=problem, batch=B, x_dtype=xd, t_gs=3, descent_cap=20, seed=3), 150)
+
+
 @pytest.mark.parametrize("xd,vd", [(1, 1), (1, 0), (2, 2), (2, 0)])
 @pytest.mark.parametrize("B", [16, 32, 128])
 def test_plain_steps_low_precision_mis(mq, xd, vd, B):
