@@ -282,6 +282,31 @@ MQO_API mqo_status mqo_spmm_grad(mqo_graph g, const float* X, const float* gout,
                          void* cuda_stream);
 
 /*
+ * Same result as mqo_spmm_grad, but the call allocates nothing.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc during the call -- code issuing work while a stream is being
+ * captured into a CUDA graph, applications whose device memory is already
+ * held by their own pool or allocator, and loops that must not pay for an
+ * allocation.  mqo_spmm_grad keeps a scratch buffer for the partial sums of
+ * long rows and allocates (or grows) it on first use; this variant keeps
+ * those partial sums in one static device array of 4 MiB (1,048,576 32-bit
+ * words) that every GPU loading the library holds until the process exits.
+ *
+ * Limit: 64 + 2*L + C*B words must fit in that array, where L is the number
+ * of rows with more than 512 entries and C the number of their 512-entry
+ * chunks; larger requests return MQO_EINVAL with the required size in
+ * mqo_last_error() and launch nothing.  B is a power of two in [1, 256].
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call on a device shares the same array: calls
+ * whose work overlaps on the GPU (on different streams without ordering)
+ * race and give wrong results; calls ordered on one stream are safe.
+ * Arguments, layouts and the returned gradient are those of mqo_spmm_grad.
+ */
+MQO_API mqo_status mqo_spmm_grad_static(mqo_graph g, const float* X, const float* gout, float* G, int32_t B,
+                                        float lambda_, void* cuda_stream);
+
+/*
  * Projected optimiser updates on device float32 arrays of length count,
  * ascending along grad and projecting onto [lo, hi] (the PGA update of
  * Sec. 3 with momentum or Adam):

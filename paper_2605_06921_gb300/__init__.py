@@ -91,6 +91,7 @@ _SIGS = {
     "mqo_objective_f64": [_P, _P],
     "mqo_fb_forward": [_P, _P, C.c_int32, C.c_float, _P, _P],
     "mqo_spmm_grad": [_P, _P, _P, _P, C.c_int32, C.c_float, _P],
+    "mqo_spmm_grad_static": [_P, _P, _P, _P, C.c_int32, C.c_float, _P],
     "mqo_pga_momentum_step": [_P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, _P],
     "mqo_pga_adam_step": [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int64,
                           C.c_float, C.c_float, _P],
@@ -328,6 +329,19 @@ def spmm_grad(graph: Graph, X, lambda_: float, gout=None):
     G = torch.empty_like(X)
     g = None if gout is None else gout.to(torch.float32).contiguous()
     _check(lib().mqo_spmm_grad(graph.handle, _dptr(X), _dptr(g), _dptr(G), B, float(lambda_), _stream()))
+    return G
+
+
+def spmm_grad_static(graph: Graph, X, lambda_: float, gout=None, out=None):
+    """As spmm_grad, through the allocation-free entry point: the library
+    allocates nothing (partial sums go to its static scratch array), and the
+    output tensor may be passed in by a caller that manages its own memory."""
+    import torch
+    X = X.contiguous()
+    B = X.shape[1]
+    G = torch.empty_like(X) if out is None else out
+    g = None if gout is None else gout.to(torch.float32).contiguous()
+    _check(lib().mqo_spmm_grad_static(graph.handle, _dptr(X), _dptr(g), _dptr(G), B, float(lambda_), _stream()))
     return G
 
 

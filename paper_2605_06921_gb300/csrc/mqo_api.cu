@@ -355,6 +355,29 @@ cudaError_t capture(mqo_solver s, int ticks, cudaGraphExec_t* out) {
 
 }  // namespace
 
+void graph_csr_view(mqo_graph_s* g, GraphCsrView* out) {
+  out->row_ptr = g->d_rp;
+  out->col = g->d_col;
+  out->w = g->d_w;
+  out->n = (int32_t)g->n;
+  int32_t rows = 0;
+  int64_t chunks = 0;
+  for (int64_t v = 0; v < g->n; ++v) {
+    const int32_t d = g->h_rp[(size_t)v + 1] - g->h_rp[(size_t)v];
+    if (d > 512) {
+      rows += 1;
+      chunks += (d + 511) / 512;
+    }
+  }
+  out->long_rows = rows;
+  out->long_chunks = chunks;
+}
+
+mqo_status set_last_error(mqo_status status, const char* msg) {
+  g_err = msg;
+  return status;
+}
+
 extern "C" {
 
 const char* mqo_last_error(void) { return g_err.c_str(); }

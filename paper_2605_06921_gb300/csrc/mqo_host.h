@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/mqo.h"
 #include "mqo_dev.cuh"
 
 namespace mqo {
@@ -48,4 +49,19 @@ cudaError_t launch_momentum(float* x, float* v, const float* grad, int64_t n, fl
 cudaError_t launch_adam(float* x, float* m, float* u, const float* grad, int64_t n, float lr, float b1, float b2,
                         float eps, int64_t t, float lo, float hi, cudaStream_t stream);
 
+// read-only view of a graph's device CSR and its long-row statistics
+// (rows longer than 512 entries, and their 512-entry chunks)
+struct GraphCsrView {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const int8_t* w;
+  int32_t n;
+  int32_t long_rows;
+  int64_t long_chunks;
+};
+
 }  // namespace mqo
+
+struct mqo_graph_s;
+void graph_csr_view(mqo_graph_s* g, mqo::GraphCsrView* out);
+mqo_status set_last_error(mqo_status status, const char* msg);
