@@ -200,6 +200,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+def aggregate_ranks(ms_local: float, units_local: float, dist=None, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (max over ranks) and the units processed by all ranks together."""
+    import torch
+    if dist is None:
+        return ms_local, units_local / (ms_local / 1e3)
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+    mx = t[:1].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = t[1:].clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms = float(mx.item())
+    return ms, float(tot.item()) / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def algorithmic_bytes_per_step(G, B, sx, sv):
     """col_idx + row_ptr read once, x read + written, momentum read + written,
@@ -289,11 +305,7 @@ def gpu_arm(args):
 
     nnz_b = G.nnz * B
     ms, step_avg_ms, clocks, best_vals = measure(xd, vd, args.steps, args.warmup, True)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = nnz_b * args.steps * world / (ms / 1e3)
+    ms, value = aggregate_ranks(ms, float(nnz_b) * args.steps, dist, "cuda")
 
     # the plain FP32-state form of the same workload, for comparison
     f32 = None
@@ -318,12 +330,9 @@ def gpu_arm(args):
     t_e2e = time.perf_counter() - t0
     s.close()
     g.close()
-    t_t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
-    t_e2e = float(t_t.item())
+    ms_e2e, e2e_value = aggregate_ranks(t_e2e * 1e3, float(nnz_b) * e2e_steps, dist, "cuda")
     csr_bytes = G.nnz * 4 + (G.n + 1) * 8 + (G.nnz if G.weights is not None else 0) + 8 * (G.num_graphs + 1)
-    e2e = {"value": nnz_b * e2e_steps * world / t_e2e, "unit": UNIT,
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(csr_bytes / e2e_steps), "d2h_bytes_per_step": int(8 * G.num_graphs * B)}
 
     alg = algorithmic_bytes_per_step(G, B, sx, sv)
