@@ -226,12 +226,14 @@ MQO_API mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds);
 
 /*
  * As mqo_run, but the ticks are enqueued one by one (no CUDA graph) with a
- * pair of CUDA events around every fused-step launch on the solver's
- * stream; synchronises and writes the summed duration of the step-kernel
- * launches (milliseconds) to *step_ms and the number of launches to
- * *launches (either may be NULL).  Used for profiling the dominant kernel.
+ * CUDA event between consecutive kernel launches on the solver's stream;
+ * synchronises and writes, summed over the nticks ticks, the milliseconds
+ * spent in each of the tick's seven kernels to phase_ms[7] (control, apply,
+ * fused step, discrete pass A, pass B, count pass C, tick end), and the
+ * number of kernel launches to *launches (either pointer may be NULL).
+ * Used to profile the tick kernel by kernel.
  */
-MQO_API mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* step_ms, int64_t* launches);
+MQO_API mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t* launches);
 
 /* mqo_init followed by mqo_run(s, nticks). */
 MQO_API mqo_status mqo_solve(mqo_solver s, int64_t nticks);

@@ -221,11 +221,14 @@ class Solver:
     def run(self, nticks):
         _check(lib().mqo_run(self.handle, int(nticks)))
 
+    PHASES = ("ctrl", "apply", "step", "disc_a", "disc_b", "disc_c", "tick_end")
+
     def run_timed(self, nticks):
-        """Run nticks ticks; returns (summed step-kernel ms, step launches)."""
-        ms, k = C.c_double(), C.c_int64()
-        _check(lib().mqo_run_timed(self.handle, int(nticks), C.byref(ms), C.byref(k)))
-        return ms.value, k.value
+        """Run nticks ticks kernel by kernel; returns ({phase: summed ms}, kernel launches)."""
+        ms = (C.c_double * 7)()
+        k = C.c_int64()
+        _check(lib().mqo_run_timed(self.handle, int(nticks), ms, C.byref(k)))
+        return dict(zip(self.PHASES, list(ms))), k.value
 
     def solve(self, nticks):
         _check(lib().mqo_solve(self.handle, int(nticks)))

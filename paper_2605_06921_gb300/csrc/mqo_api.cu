@@ -584,10 +584,11 @@ mqo_status mqo_run(mqo_solver s, int64_t nticks) {
   return MQO_OK;
 }
 
-mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* step_ms, int64_t* launches) {
+mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t* launches) {
   CHECK_SOLVER(s);
   if (nticks < 0) return fail(MQO_EINVAL, "nticks < 0");
-  std::vector<cudaEvent_t> ev((size_t)2 * nticks);
+  constexpr int kPhases = 7;
+  std::vector<cudaEvent_t> ev((size_t)(kPhases + 1) * nticks);
   for (auto& e : ev) CKS(cudaEventCreate(&e));
   cudaError_t err = cudaSuccess;
   {
@@ -595,27 +596,39 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* step_ms, int64_t*
     const SolverDev& S = s->S;
     const int G = S.g.num_graphs;
     for (int64_t k = 0; k < nticks && err == cudaSuccess; ++k) {
-      err = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
+      cudaEvent_t* e = &ev[(size_t)(kPhases + 1) * k];
+      int i = 0;
+      err = cudaEventRecord(e[i++], s->work);
+      if (err == cudaSuccess) err = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
+      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
       if (err == cudaSuccess) err = launch_apply(S, s->work);
-      if (err == cudaSuccess) err = cudaEventRecord(ev[(size_t)2 * k], s->work);
+      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
       if (err == cudaSuccess) err = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
-      if (err == cudaSuccess) err = cudaEventRecord(ev[(size_t)2 * k + 1], s->work);
-      for (int pass = 0; pass < 3 && err == cudaSuccess; ++pass) err = launch_disc(S, pass, s->work);
+      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
+      for (int pass = 0; pass < 3 && err == cudaSuccess; ++pass) {
+        err = launch_disc(S, pass, s->work);
+        if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
+      }
       if (err == cudaSuccess) err = launch_tick_end(S, s->work);
+      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
     }
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s->work);
-  double total = 0.0;
+  double tot[kPhases] = {0};
   for (int64_t k = 0; k < nticks && err == cudaSuccess; ++k) {
-    float ms = 0.0f;
-    err = cudaEventElapsedTime(&ms, ev[(size_t)2 * k], ev[(size_t)2 * k + 1]);
-    total += ms;
+    const cudaEvent_t* e = &ev[(size_t)(kPhases + 1) * k];
+    for (int p = 0; p < kPhases && err == cudaSuccess; ++p) {
+      float ms = 0.0f;
+      err = cudaEventElapsedTime(&ms, e[p], e[p + 1]);
+      tot[p] += ms;
+    }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return poison(s, err, "mqo_run_timed");
   s->host_tick += nticks;
-  if (step_ms) *step_ms = total;
-  if (launches) *launches = nticks;
+  if (phase_ms)
+    for (int p = 0; p < kPhases; ++p) phase_ms[p] = tot[p];
+  if (launches) *launches = (int64_t)kPhases * nticks;
   return MQO_OK;
 }
 

@@ -23,7 +23,8 @@
 // k_step_s: member graphs small enough for shared memory: the CTA first
 //   copies its graph's block of x (and, for MIS, of the rounding bits) to
 //   shared memory; every neighbour gather then hits shared memory, and the
-//   MIS checker ORs whole 32-trajectory words of neighbour bits.
+//   MIS checker ORs whole 32-trajectory words of neighbour bits.  Several
+//   rows per warp share each shuffle and shared-memory instruction.
 #include "mqo_dev.cuh"
 #include "mqo_host.h"
 
@@ -229,11 +230,16 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
 }
 
 // ---------------------------------------------------------------- shared memory
-// B >= 32: one warp per row (LPR = 32), VEC = B/32 trajectories per lane, so
-// the bit words of a node are VEC words and lane l's bits lie in word
-// (l*VEC)/32.
-template <typename TX, typename TV, int VEC, bool MIS>
-__global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
+// Each lane owns VEC consecutive trajectories (8 or 16 bytes of x), a row
+// group of LPR = B/VEC lanes one node, and the RPW = 32/LPR row groups of a
+// warp walk their rows' neighbour lists in lockstep (to the longest list in
+// the warp, shorter rows idle), so one shuffle and one shared-memory load
+// instruction serve RPW rows.  DUP (64-byte rows): the graph's block of x is
+// stored with a 128-byte pitch and each row twice, bytes [0,64) and
+// [64,128); row groups of odd index read the second copy, so the two row
+// groups of a half-warp always use opposite halves of the 32 banks.
+template <typename TX, typename TV, int VEC, bool MIS, bool DUP>
+__global__ void __launch_bounds__(256) k_step_s(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int it = blockIdx.x;
   const Item item = a.g.items[it];
@@ -241,11 +247,12 @@ __global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
   const int64_t t = *a.tick;
   if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
   const int B = a.B;
-  constexpr int BW = VEC;  // words per node
+  const int BW = a.Bw;
   const int32_t off = a.g.node_off[g];
   const int32_t ng = a.g.node_off[g + 1] - off;
-  TX* sX = reinterpret_cast<TX*>(smem);
-  const size_t xbytes = ((size_t)ng * B * sizeof(TX) + 15) & ~(size_t)15;
+  const int rowb = B * (int)sizeof(TX);           // bytes of one node's x
+  const int pitch = DUP ? 128 : rowb;
+  const size_t xbytes = ((size_t)ng * pitch + 15) & ~(size_t)15;
   uint32_t* sZ = reinterpret_cast<uint32_t*>(smem + xbytes);
   const size_t zbytes = MIS ? (((size_t)ng * BW * 4 + 15) & ~(size_t)15) : 0;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem + xbytes + zbytes);
@@ -259,9 +266,15 @@ __global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
   // stage the member graph's x block (16-byte copies) and rounding words
   {
     const int4* src = reinterpret_cast<const int4*>(Xc + (int64_t)off * B);
-    int4* dst = reinterpret_cast<int4*>(sX);
-    const int n16 = (int)(((size_t)ng * B * sizeof(TX)) / 16);
-    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    const int per = rowb / 16;  // 16-byte pieces per node
+    const int n16 = ng * per;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+      const int4 vv = src[i];
+      const int node = i / per, piece = i - node * per;
+      unsigned char* d = smem + (size_t)node * pitch + piece * 16;
+      *reinterpret_cast<int4*>(d) = vv;
+      if (DUP) *reinterpret_cast<int4*>(d + 64) = vv;
+    }
     if (MIS) {
       const uint32_t* zs = Zc + (int64_t)off * BW;
       for (int i = threadIdx.x; i < ng * BW; i += blockDim.x) sZ[i] = zs[i];
@@ -270,8 +283,12 @@ __global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
   }
   __syncthreads();
 
+  const int lpr = B / VEC;
+  const int rpw = 32 / lpr;
   const int lane = threadIdx.x & 31;
-  const int b0 = lane * VEC;
+  const int sub = lane / lpr;
+  const int l = lane - sub * lpr;
+  const int b0 = l * VEC;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const float thr = MIS ? 0.5f : 0.0f;
@@ -280,7 +297,9 @@ __global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
   const int32_t* __restrict__ rp = a.g.row_ptr;
   const int32_t* __restrict__ col = a.g.col;
   const int8_t* __restrict__ wts = a.g.w;
-  constexpr int K = 32 / VEC;
+  const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;  // lanes sharing one output word
+  const unsigned rmask = lpr == 32 ? 0xffffffffu : (((1u << lpr) - 1u) << (sub * lpr));
+  const unsigned char* sXl = smem + (DUP ? (sub & 1) * 64 : 0) + l * (VEC * (int)sizeof(TX));
 
   bool stepping[VEC];
 #pragma unroll
@@ -289,70 +308,71 @@ __global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
 #pragma unroll
   for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
 
-  for (int v = item.v0 + warp; v < item.v1; v += nwarps) {
-    const int vl = v - off;
-    const int64_t base = (int64_t)v * B + b0;
-    const Pack<TX, VEC> xv = ld_pack<TX, VEC>(sX + (int64_t)vl * B + b0);
-    const Pack<TV, VEC> vv = ld_pack_stream<TV, VEC>(V + base);
+  // rows of this item, RPW per warp per pass; the warp loops while any of
+  // its row groups has a row
+  for (int vb = item.v0 + warp * rpw; vb < item.v1; vb += nwarps * rpw) {
+    const int v = vb + sub;
+    const bool has = v < item.v1;
+    const int vl = has ? v - off : 0;
+    const int64_t base = (int64_t)(has ? v : item.v0) * B + b0;
+    const Pack<TX, VEC> xv = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)vl * pitch);
+    Pack<TV, VEC> vv{};
+    if (has) vv = ld_pack_stream<TV, VEC>(V + base);
     float acc[VEC];
     int pos[VEC];
-    uint32_t orw[BW];
+    uint32_t orw[4] = {0u, 0u, 0u, 0u};  // OR of the neighbours' words (BW <= 4)
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; orw[e] = 0u; }
-    const int rs = rp[v], re = rp[v + 1];
+    for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
+    const int rs = has ? rp[v] : 0, re = has ? rp[v + 1] : 0;
+    const int nch = (re - rs + lpr - 1) / lpr;
+    const int nch_w = __reduce_max_sync(0xffffffffu, nch);
     int wsum = 0;
-    for (int cb = rs; cb < re; cb += 32) {
-      const int j = cb + lane;
-      const int myu = j < re ? __ldcs(col + j) - off : 0;
-      const int myw = (weighted && j < re) ? (int)wts[j] : 1;
-      if (MIS && j < re) {
-#pragma unroll
+    for (int ch = 0; ch < nch_w; ++ch) {
+      const int cb = rs + ch * lpr;
+      const int j = cb + l;
+      const bool jin = j < re;
+      const int myu = jin ? __ldcs(col + j) - off : 0;
+      const int myw = (weighted && jin) ? (int)wts[j] : 1;
+      if (MIS && jin) {
         for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu * BW + w];
       }
-      const int cnt = min(32, re - cb);
-      int k = 0;
-      for (; k + 8 <= cnt; k += 8) {
-        int u[8], w[8];
-        Pack<TX, VEC> p[8];
+      const int cnt = max(0, min(lpr, re - cb));
+      const int cnt_w = __reduce_max_sync(0xffffffffu, cnt);
+      for (int k = 0; k < cnt_w; k += 4) {
+        int u[4], w[4];
+        Pack<TX, VEC> p[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          u[q] = __shfl_sync(0xffffffffu, myu, k + q);
-          w[q] = weighted ? __shfl_sync(0xffffffffu, myw, k + q) : 1;
+        for (int q = 0; q < 4; ++q) {
+          u[q] = __shfl_sync(0xffffffffu, myu, k + q, lpr);
+          w[q] = weighted ? __shfl_sync(0xffffffffu, myw, k + q, lpr) : 1;
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) p[q] = ld_pack<TX, VEC>(sX + u[q] * B + b0);
+        for (int q = 0; q < 4; ++q) p[q] = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)u[q] * pitch);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          wsum += w[q];
+        for (int q = 0; q < 4; ++q) {
+          if (k + q < cnt) {
+            wsum += w[q];
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            const float f = to_f(p[q].e[e]);
-            acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
-            if (!MIS) pos[e] += (f > thr) ? w[q] : 0;
+            for (int e = 0; e < VEC; ++e) {
+              const float f = to_f(p[q].e[e]);
+              acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
+              if (!MIS) pos[e] += (f > thr) ? w[q] : 0;
+            }
           }
-        }
-      }
-      for (; k < cnt; ++k) {
-        const int u = __shfl_sync(0xffffffffu, myu, k);
-        const int w = weighted ? __shfl_sync(0xffffffffu, myw, k) : 1;
-        const Pack<TX, VEC> p = ld_pack<TX, VEC>(sX + u * B + b0);
-        wsum += w;
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const float f = to_f(p.e[e]);
-          acc[e] = w >= 0 ? acc[e] + f : acc[e] - f;
-          if (!MIS) pos[e] += (f > thr) ? w : 0;
         }
       }
     }
     if (MIS) {
+      for (int w = 0; w < BW; ++w)
+        for (int o = 1; o < lpr; o <<= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
 #pragma unroll
-      for (int w = 0; w < BW; ++w) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
+      for (int e = 0; e < VEC; ++e) {
+        const int bb = b0 + e;
+        uint32_t word = orw[0];
+        for (int w = 1; w < BW; ++w)
+          if ((bb >> 5) == w) word = orw[w];
+        pos[e] = (word >> (bb & 31)) & 1u;
       }
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) pos[e] = (orw[(b0 + e) >> 5] >> ((b0 + e) & 31)) & 1u;
     }
     Pack<TX, VEC> xo;
     Pack<TV, VEC> vo;
@@ -360,50 +380,78 @@ __global__ void __launch_bounds__(512) k_step_s(StepArgs a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       bool zn;
+      int d0 = 0, d1 = 0, d2 = 0;
       step_element<TX, TV>(a, MIS, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, stepping[e], xo.e[e], vo.e[e],
-                           zn, c0[e], c1[e], c2[e]);
+                           zn, d0, d1, d2);
+      if (has) {
+        c0[e] += d0;
+        c1[e] += d1;
+        c2[e] += d2;
+      }
       zbits |= (unsigned)zn << e;
     }
-    st_pack<TX, VEC>(Xn + base, xo);
-    st_pack<TV, VEC>(V + base, vo);
+    if (has) {
+      st_pack<TX, VEC>(Xn + base, xo);
+      st_pack<TV, VEC>(V + base, vo);
+    }
     unsigned word = zbits << (b0 & 31);
-#pragma unroll
-    for (int o = 1; o < K; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
-    if ((lane % K) == 0) Zn[(int64_t)v * BW + (b0 >> 5)] = word;
+    for (int o = 1; o < K; o <<= 1) word |= __shfl_xor_sync(rmask, word, o);
+    if (has && (l % K) == 0) Zn[(int64_t)v * BW + (b0 >> 5)] = word;
   }
   flush_step_counters<VEC>(a, s_cnt, g, it, b0, c0, c1, c2, stepping);
 }
 
+// lanes hold 8 bytes of x (or B/32 elements if more), so VEC = max(8/sx, B/32)
+static int smem_vec(int B, int x_dtype) {
+  const int sx = x_dtype == DT_F32 ? 4 : 2;
+  const int v8 = 8 / sx;
+  return B / 32 > v8 ? B / 32 : v8;
+}
+
 size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng) {
   const size_t sx = x_dtype == DT_F32 ? 4 : 2;
-  const size_t xb = ((size_t)max_ng * B * sx + 15) & ~(size_t)15;
+  const size_t rowb = (size_t)B * sx;
+  const size_t pitch = rowb == 64 ? 128 : rowb;
+  const size_t xb = ((size_t)max_ng * pitch + 15) & ~(size_t)15;
   const size_t zb = problem == PROB_MIS ? (((size_t)max_ng * ((B + 31) / 32) * 4 + 15) & ~(size_t)15) : 0;
   return xb + zb + 3 * (size_t)B * 8;
 }
 
-template <typename TX, typename TV, int VEC>
-static cudaError_t launch_vec(bool smem_path, size_t smem, bool mis, const StepArgs& a, int grid, cudaStream_t s) {
-  if (smem_path) {
-    if (mis) {
-      cudaFuncSetAttribute(k_step_s<TX, TV, VEC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_step_s<TX, TV, VEC, true><<<grid, 512, smem, s>>>(a);
-    } else {
-      cudaFuncSetAttribute(k_step_s<TX, TV, VEC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_step_s<TX, TV, VEC, false><<<grid, 512, smem, s>>>(a);
-    }
+template <typename TX, typename TV, int VEC, bool MIS>
+static cudaError_t launch_s(size_t smem, bool dup, const StepArgs& a, int grid, cudaStream_t s) {
+  if (dup) {
+    cudaFuncSetAttribute(k_step_s<TX, TV, VEC, MIS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_step_s<TX, TV, VEC, MIS, true><<<grid, 256, smem, s>>>(a);
   } else {
-    k_step_g<TX, TV, VEC><<<grid, 256, 0, s>>>(a);
+    cudaFuncSetAttribute(k_step_s<TX, TV, VEC, MIS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_step_s<TX, TV, VEC, MIS, false><<<grid, 256, smem, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+template <typename TX, typename TV>
+static cudaError_t launch_smem(int B, size_t smem, bool mis, const StepArgs& a, int grid, cudaStream_t s) {
+  const int vec = smem_vec(B, sizeof(TX) == 4 ? DT_F32 : DT_BF16);
+  const bool dup = B * (int)sizeof(TX) == 64;
+  if (vec == 2) return mis ? launch_s<TX, TV, 2, true>(smem, dup, a, grid, s) : launch_s<TX, TV, 2, false>(smem, dup, a, grid, s);
+  if (vec == 4) return mis ? launch_s<TX, TV, 4, true>(smem, dup, a, grid, s) : launch_s<TX, TV, 4, false>(smem, dup, a, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename TX, typename TV, int VEC>
+static cudaError_t launch_vec(const StepArgs& a, int grid, cudaStream_t s) {
+  k_step_g<TX, TV, VEC><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename TX, typename TV>
 static cudaError_t launch_tv(int vec, bool smem_path, size_t smem, bool mis, const StepArgs& a, int grid,
                              cudaStream_t s) {
+  if (smem_path) return launch_smem<TX, TV>(a.B, smem, mis, a, grid, s);
   switch (vec) {
-    case 1: return launch_vec<TX, TV, 1>(smem_path, smem, mis, a, grid, s);
-    case 2: return launch_vec<TX, TV, 2>(smem_path, smem, mis, a, grid, s);
-    case 4: return launch_vec<TX, TV, 4>(smem_path, smem, mis, a, grid, s);
+    case 1: return launch_vec<TX, TV, 1>(a, grid, s);
+    case 2: return launch_vec<TX, TV, 2>(a, grid, s);
+    case 4: return launch_vec<TX, TV, 4>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
