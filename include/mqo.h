@@ -225,8 +225,8 @@ MQO_API mqo_status mqo_evaluate(mqo_solver s, const uint32_t* z_bits, int64_t* v
 MQO_API mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds);
 
 /*
- * As mqo_run, but the ticks are enqueued one by one (no CUDA graph) with a
- * CUDA event between consecutive kernel launches on the solver's stream;
+ * As mqo_run, with the nticks ticks captured as one CUDA graph that holds
+ * an event-record node between consecutive kernels on the solver's stream;
  * synchronises and writes, summed over the nticks ticks, the milliseconds
  * spent in each of the tick's seven kernels to phase_ms[7] (control, apply,
  * fused step, discrete pass A, pass B, count pass C, tick end), and the

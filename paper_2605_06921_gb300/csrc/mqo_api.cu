@@ -592,26 +592,38 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t
   for (auto& e : ev) CKS(cudaEventCreate(&e));
   cudaError_t err = cudaSuccess;
   {
+    // the nticks ticks are captured as one CUDA graph (as mqo_run replays
+    // them) with an event-record node between consecutive kernels
     Scope sc(s);
     const SolverDev& S = s->S;
     const int G = S.g.num_graphs;
-    for (int64_t k = 0; k < nticks && err == cudaSuccess; ++k) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    err = cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal);
+    cudaError_t ek = cudaSuccess;
+    for (int64_t k = 0; k < nticks && err == cudaSuccess && ek == cudaSuccess; ++k) {
       cudaEvent_t* e = &ev[(size_t)(kPhases + 1) * k];
       int i = 0;
-      err = cudaEventRecord(e[i++], s->work);
-      if (err == cudaSuccess) err = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
-      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
-      if (err == cudaSuccess) err = launch_apply(S, s->work);
-      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
-      if (err == cudaSuccess) err = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
-      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
-      for (int pass = 0; pass < 3 && err == cudaSuccess; ++pass) {
-        err = launch_disc(S, pass, s->work);
-        if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
+      ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = launch_apply(S, s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      for (int pass = 0; pass < 3 && ek == cudaSuccess; ++pass) {
+        ek = launch_disc(S, pass, s->work);
+        if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
       }
-      if (err == cudaSuccess) err = launch_tick_end(S, s->work);
-      if (err == cudaSuccess) err = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = launch_tick_end(S, s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
     }
+    if (err == cudaSuccess) err = cudaStreamEndCapture(s->work, &graph);
+    if (err == cudaSuccess) err = ek;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+    if (err == cudaSuccess) err = cudaGraphLaunch(exec, s->work);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
   }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s->work);
   double tot[kPhases] = {0};

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
 // [64,128); row groups of odd index read the second copy, so the two row
 // groups of a half-warp always use opposite halves of the 32 banks.
 template <typename TX, typename TV, int VEC, bool MIS, bool DUP>
-__global__ void __launch_bounds__(256) k_step_s(StepArgs a) {
+__global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int it = blockIdx.x;
   const Item item = a.g.items[it];
@@ -327,36 +327,50 @@ __global__ void __launch_bounds__(256) k_step_s(StepArgs a) {
     const int nch = (re - rs + lpr - 1) / lpr;
     const int nch_w = __reduce_max_sync(0xffffffffu, nch);
     int wsum = 0;
-    for (int ch = 0; ch < nch_w; ++ch) {
-      const int cb = rs + ch * lpr;
-      const int j = cb + l;
-      const bool jin = j < re;
-      const int myu = jin ? __ldcs(col + j) - off : 0;
-      const int myw = (weighted && jin) ? (int)wts[j] : 1;
-      if (MIS && jin) {
-        for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu * BW + w];
+    // column indices of four chunks are loaded before any of them is used
+    for (int ch0 = 0; ch0 < nch_w; ch0 += 4) {
+      int myu[4], myw[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = rs + (ch0 + c) * lpr + l;
+        const bool jin = j < re;
+        myu[c] = jin ? __ldcs(col + j) - off : 0;
+        myw[c] = (weighted && jin) ? (int)wts[j] : 1;
       }
-      const int cnt = max(0, min(lpr, re - cb));
-      const int cnt_w = __reduce_max_sync(0xffffffffu, cnt);
-      for (int k = 0; k < cnt_w; k += 4) {
-        int u[4], w[4];
-        Pack<TX, VEC> p[4];
+      if (MIS) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          u[q] = __shfl_sync(0xffffffffu, myu, k + q, lpr);
-          w[q] = weighted ? __shfl_sync(0xffffffffu, myw, k + q, lpr) : 1;
+        for (int c = 0; c < 4; ++c) {
+          if (rs + (ch0 + c) * lpr + l < re) {
+            for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu[c] * BW + w];
+          }
         }
+      }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) p[q] = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)u[q] * pitch);
+      for (int c = 0; c < 4; ++c) {
+        const int cb = rs + (ch0 + c) * lpr;
+        const int cnt = max(0, min(lpr, re - cb));
+        const int cnt_w = __reduce_max_sync(0xffffffffu, cnt);
+        if (cnt_w == 0) break;
+        for (int k = 0; k < cnt_w; k += 4) {
+          int u[4], w[4];
+          Pack<TX, VEC> p[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (k + q < cnt) {
-            wsum += w[q];
+          for (int q = 0; q < 4; ++q) {
+            u[q] = __shfl_sync(0xffffffffu, myu[c], k + q, lpr);
+            w[q] = weighted ? __shfl_sync(0xffffffffu, myw[c], k + q, lpr) : 1;
+          }
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-              const float f = to_f(p[q].e[e]);
-              acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
-              if (!MIS) pos[e] += (f > thr) ? w[q] : 0;
+          for (int q = 0; q < 4; ++q) p[q] = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)u[q] * pitch);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (k + q < cnt) {
+              wsum += w[q];
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) {
+                const float f = to_f(p[q].e[e]);
+                acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
+                if (!MIS) pos[e] += (f > thr) ? w[q] : 0;
+              }
             }
           }
         }
@@ -421,10 +435,10 @@ template <typename TX, typename TV, int VEC, bool MIS>
 static cudaError_t launch_s(size_t smem, bool dup, const StepArgs& a, int grid, cudaStream_t s) {
   if (dup) {
     cudaFuncSetAttribute(k_step_s<TX, TV, VEC, MIS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_step_s<TX, TV, VEC, MIS, true><<<grid, 256, smem, s>>>(a);
+    k_step_s<TX, TV, VEC, MIS, true><<<grid, 512, smem, s>>>(a);
   } else {
     cudaFuncSetAttribute(k_step_s<TX, TV, VEC, MIS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_step_s<TX, TV, VEC, MIS, false><<<grid, 256, smem, s>>>(a);
+    k_step_s<TX, TV, VEC, MIS, false><<<grid, 512, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
