@@ -604,19 +604,19 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t
     for (int64_t k = 0; k < nticks && err == cudaSuccess && ek == cudaSuccess; ++k) {
       cudaEvent_t* e = &ev[(size_t)(kPhases + 1) * k];
       int i = 0;
-      ek = cudaEventRecord(e[i++], s->work);
+      ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       if (ek == cudaSuccess) ek = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
-      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       if (ek == cudaSuccess) ek = launch_apply(S, s->work);
-      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       if (ek == cudaSuccess) ek = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
-      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       for (int pass = 0; pass < 3 && ek == cudaSuccess; ++pass) {
         ek = launch_disc(S, pass, s->work);
-        if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+        if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       }
       if (ek == cudaSuccess) ek = launch_tick_end(S, s->work);
-      if (ek == cudaSuccess) ek = cudaEventRecord(e[i++], s->work);
+      if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
     }
     if (err == cudaSuccess) err = cudaStreamEndCapture(s->work, &graph);
     if (err == cudaSuccess) err = ek;

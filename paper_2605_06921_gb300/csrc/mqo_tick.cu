@@ -288,59 +288,77 @@ __device__ __forceinline__ uint32_t group_nb_or(const SolverDev& S, const uint32
 }
 
 // ---------------------------------------------------------------- apply
+// Each CTA (one item) first lists the trajectories of its member graph that
+// have an apply action this tick, then visits only those (node, trajectory)
+// pairs, node fastest.  Bit updates are atomic (several listed trajectories
+// may touch the same node's word).
+__device__ __forceinline__ void set_bit_atomic(uint32_t* words, int64_t v, int Bw, int b, bool val) {
+  uint32_t* wp = words + v * Bw + (b >> 5);
+  const uint32_t bit = 1u << (b & 31);
+  if (val) atomicOr(wp, bit);
+  else atomicAnd(wp, ~bit);
+}
+
 __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
+  __shared__ int s_list[128];
+  __shared__ int s_n;
   const int it = blockIdx.x;
   const int64_t t = *S.tick;
   if (S.any[0] != (int32_t)(t + 1)) return;
   const Item item = S.g.items[it];
   if (S.gflag[item.g] != (int32_t)(t + 1)) return;
   const int B = S.B, Bw = S.Bw;
+  const int g = item.g;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x)
+    if (S.act[(int64_t)g * B + b] & ACT_APPLY_MASK) s_list[atomicAdd(&s_n, 1)] = b;
+  __syncthreads();
+  const int nact = s_n;
+  const int nodes = item.v1 - item.v0;
   const bool mis = S.p.problem == PROB_MIS;
   const float thr = mis ? 0.5f : 0.0f;
   void* Xc = (t & 1) ? S.X1 : S.X0;
   uint32_t* Zc = (t & 1) ? S.ZX1 : S.ZX0;
   const uint32_t* Zp = (t & 1) ? S.ZX0 : S.ZX1;  // rounding of the x the last step evaluated
-  item_pairs(S, item, [&](const PairCtx& c) {
-    const int64_t v = c.v;
-    const int b = c.b;
-    const int act = c.in ? S.act[c.tau] : 0;
-    const bool acc_zx = act & ACT_ACC_ZX, acc_w = act & ACT_ACC_WORK;
-    bool zb = false;
-    if (c.in) zb = get_bit(S.Zbest, v, Bw, b);
-    bool src = false;
-    if (acc_zx) src = get_bit(Zp, v, Bw, b);
-    if (acc_w) src = get_bit(S.Zwork, v, Bw, b);
-    const bool acc = acc_zx || acc_w;
-    if (acc) zb = src;
-    update_word(S.Zbest, v, Bw, b, B, src, acc);
-    bool wv = false;
-    if (act & ACT_WORK_ZX) wv = get_bit(Zp, v, Bw, b);
-    if (act & ACT_WORK_BEST) wv = zb;
-    update_word(S.Zwork, v, Bw, b, B, wv, (act & (ACT_WORK_ZX | ACT_WORK_BEST)) != 0);
-    const bool newx = (act & (ACT_RESET | ACT_INIT)) != 0;
-    float x = 0.0f;
-    if (newx) {
-      const int32_t off = S.g.node_off[c.g];
+  const int32_t off = S.g.node_off[g];
+  const uint32_t n_g = (uint32_t)(S.g.node_off[g + 1] - off);
+  for (int idx = threadIdx.x; idx < nact * nodes; idx += blockDim.x) {
+    const int b = s_list[idx / nodes];
+    const int64_t v = item.v0 + idx % nodes;
+    const int64_t tau = (int64_t)g * B + b;
+    const int act = S.act[tau];
+    bool zb = get_bit(S.Zbest, v, Bw, b);
+    if (act & (ACT_ACC_ZX | ACT_ACC_WORK)) {
+      const bool src = (act & ACT_ACC_ZX) ? get_bit(Zp, v, Bw, b) : get_bit(S.Zwork, v, Bw, b);
+      if (src != zb) set_bit_atomic(S.Zbest, v, Bw, b, src);
+      zb = src;
+    }
+    if (act & (ACT_WORK_ZX | ACT_WORK_BEST)) {
+      const bool wv = (act & ACT_WORK_ZX) ? get_bit(Zp, v, Bw, b) : zb;
+      set_bit_atomic(S.Zwork, v, Bw, b, wv);
+    }
+    if (act & (ACT_RESET | ACT_INIT)) {
       const uint32_t vl = (uint32_t)(v - off);
+      float x;
       if (act & ACT_RESET) {
-        const TrajState& st = S.st[c.tau];
+        const TrajState& st = S.st[tau];
         x = zb ? 1.0f : (mis ? 0.0f : -1.0f);
-        const uint32_t n_g = (uint32_t)(S.g.node_off[c.g + 1] - off);
         uint32_t keys[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) keys[i] = st.rkeys[i];
         if ((int64_t)feistel_sigma(n_g, keys, vl) < st.rk) x = 0.0f;
       } else {
         const Params& p = S.p;
-        const int32_t o = S.st[c.tau].o;
-        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)o, (uint64_t)vl, 0ULL, p.seed, (uint64_t)c.tau);
+        const int32_t o = S.st[tau].o;
+        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)o, (uint64_t)vl, 0ULL, p.seed, (uint64_t)tau);
         const float lo = mis ? 0.0f : -1.0f, hi = 1.0f;
         if (p.init_kind == 0) {
           const float u = unit24(r.v[0]);
           x = lo + (hi - lo) * u;
         } else {
           const int32_t d = S.g.row_ptr[v + 1] - S.g.row_ptr[v];
-          const int32_t dm = S.g.dmax[c.g];
+          const int32_t dm = S.g.dmax[g];
           const float q = dm > 0 ? (float)d / (float)dm : 0.0f;
           float base = 1.0f - q;
           if (!mis) base = 2.0f * base - 1.0f;
@@ -368,9 +386,9 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
       if (S.p.v_dtype == DT_F32) static_cast<float*>(S.V)[e] = 0.0f;
       else if (S.p.v_dtype == DT_BF16) static_cast<__nv_bfloat16*>(S.V)[e] = __float2bfloat16_rn(0.0f);
       else static_cast<__half*>(S.V)[e] = __float2half_rn(0.0f);
+      set_bit_atomic(Zc, v, Bw, b, x > thr);
     }
-    update_word(Zc, v, Bw, b, B, x > thr, newx);
-  });
+  }
 }
 
 cudaError_t launch_apply(const SolverDev& S, cudaStream_t stream) {
