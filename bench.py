@@ -299,12 +299,13 @@ def gpu_arm(args):
         ms = e0.elapsed_time(e1)
         clocks = sampler.summary() if sampler else None
         vals, _ = s.best(want_bits=False)
+        info = s.info()
         s.close()
         g.close()
-        return ms, phase_ms, clocks, vals
+        return ms, phase_ms, clocks, vals, info
 
     nnz_b = G.nnz * B
-    ms, phase_ms, clocks, best_vals = measure(xd, vd, args.steps, args.warmup, True)
+    ms, phase_ms, clocks, best_vals, plan = measure(xd, vd, args.steps, args.warmup, True)
     step_avg_ms = phase_ms["step"] / args.steps
     ms, value = aggregate_ranks(ms, float(nnz_b) * args.steps, dist, "cuda")
 
@@ -312,7 +313,7 @@ def gpu_arm(args):
     f32 = None
     if xd != 0 and not args.no_compare:
         k32 = max(1, args.steps // 2)
-        ms32, ph32, _, _ = measure(0, 0, k32, args.warmup, False)
+        ms32, ph32, _, _, _ = measure(0, 0, k32, args.warmup, False)
         f32 = {"value": nnz_b * k32 / (ms32 / 1e3), "ms_per_step": ms32 / k32, "step_kernel_ms": ph32["step"] / k32}
 
     # end to end through the public API with host buffers: graph upload from
@@ -337,10 +338,26 @@ def gpu_arm(args):
            "h2d_bytes_per_step": int(csr_bytes / e2e_steps), "d2h_bytes_per_step": int(8 * G.num_graphs * B)}
 
     alg = algorithmic_bytes_per_step(G, B, sx, sv)
-    achieved = alg / (step_avg_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": step_kernel_traffic(args.workload, args.x_dtype), "kernel": "mqo::k_step",
-            "step_kernel_ms": step_avg_ms, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+    hbm_achieved = alg / (step_avg_ms / 1e3) / 1e9
+    hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+           "frac": hbm_achieved / hbm_peak, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+    traffic = step_kernel_traffic(args.workload, args.x_dtype)
+    if plan["step_kernel"] == "smem":
+        # every neighbour row of x is read from shared memory once per step:
+        # nnz * B * sx bytes; peak = one 128-byte wavefront per clock per SM
+        sm_clock = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        smem_peak = 128.0 * n_sm * sm_clock * 1e6 / 1e9
+        gathered = float(G.nnz) * B * sx
+        smem_achieved = gathered / (step_avg_ms / 1e3) / 1e9
+        roof = {"bound": "smem", "achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": smem_achieved / smem_peak, "traffic": traffic,
+                "peak_derivation": f"128 B/clk/SM x {n_sm} SMs x {sm_clock:.0f} MHz (sampled SM clock)",
+                "algorithmic_bytes_per_launch": gathered, "hbm": hbm}
+    else:
+        roof = dict(hbm, traffic=traffic)
+    roof.update(kernel="mqo::k_step_s" if plan["step_kernel"] == "smem" else "mqo::k_step_g",
+                step_kernel_ms=step_avg_ms, plan=plan)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -248,6 +248,17 @@ MQO_API mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits);
 /* Per-trajectory machine state (host array of G*B mqo_traj_info).  Synchronises. */
 MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
 
+/*
+ * Execution plan chosen at creation (host, any pointer may be NULL):
+ * *step_kernel = 1 if the fused step stages each member graph's block of x
+ * in shared memory (every member graph fits), 0 for the global-memory
+ * kernel; *smem_bytes = its dynamic shared memory per CTA; *items = CTAs
+ * per step (node ranges of at most 256 nodes); *replicas = counter
+ * replicas per trajectory.
+ */
+MQO_API mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_bytes, int32_t* items,
+                                   int32_t* replicas);
+
 /* Copy the current relaxed iterate X (n*B values of x_dtype, node-major)
  * to / from device memory.  During a discrete phase a trajectory's x is
  * not defined and mqo_get_x returns stale values for it. */

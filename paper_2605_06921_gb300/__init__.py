@@ -85,6 +85,7 @@ _SIGS = {
     "mqo_run_timed": [_P, C.c_int64, _P, _P],
     "mqo_best": [_P, _P, _P],
     "mqo_traj_state": [_P, _P],
+    "mqo_solver_info": [_P, _P, _P, _P, _P],
     "mqo_get_x": [_P, _P],
     "mqo_set_x": [_P, _P],
     "mqo_get_v": [_P, _P],
@@ -265,6 +266,13 @@ class Solver:
         bits = self.bits_tensor() if want_bits else None
         _check(lib().mqo_best(self.handle, _hptr(vals), _dptr(bits)))
         return vals, bits
+
+    def info(self):
+        """Execution plan: step kernel (1 shared-memory staged, 0 global), smem bytes, items, counter replicas."""
+        k, sm, it, r = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
+        _check(lib().mqo_solver_info(self.handle, C.byref(k), C.byref(sm), C.byref(it), C.byref(r)))
+        return {"step_kernel": "smem" if k.value else "global", "smem_bytes": sm.value, "items": it.value,
+                "replicas": r.value}
 
     def traj_state(self):
         arr = (TrajInfo * self.T)()

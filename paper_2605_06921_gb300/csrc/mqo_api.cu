@@ -768,6 +768,16 @@ mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits) {
   return MQO_OK;
 }
 
+mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_bytes, int32_t* items,
+                           int32_t* replicas) {
+  if (!s) return fail(MQO_EINVAL, "null solver");
+  if (step_kernel) *step_kernel = s->step_smem > 0 ? 1 : 0;
+  if (smem_bytes) *smem_bytes = (int64_t)s->step_smem;
+  if (items) *items = s->S.g.num_items;
+  if (replicas) *replicas = s->S.R;
+  return MQO_OK;
+}
+
 mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
   CHECK_SOLVER(s);
   if (!out) return fail(MQO_EINVAL, "null out");

@@ -232,15 +232,21 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
 // ---------------------------------------------------------------- shared memory
 // Each lane owns VEC consecutive trajectories (8 or 16 bytes of x), a row
 // group of LPR = B/VEC lanes one node, and the RPW = 32/LPR row groups of a
-// warp walk their rows' neighbour lists in lockstep (to the longest list in
-// the warp, shorter rows idle), so one shuffle and one shared-memory load
-// instruction serve RPW rows.  DUP (64-byte rows): the graph's block of x is
-// stored with a 128-byte pitch and each row twice, bytes [0,64) and
-// [64,128); row groups of odd index read the second copy, so the two row
-// groups of a half-warp always use opposite halves of the 32 banks.
-template <typename TX, typename TV, int VEC, bool MIS, bool DUP>
+// warp walk their rows' neighbour lists in lockstep, LPR neighbours (one
+// chunk) at a time, so one shuffle and one shared-memory load instruction
+// serve RPW rows.  Rows shorter than the warp's longest are padded with a
+// dummy neighbour, local index ng, whose shared-memory row of x and bit
+// words are zero: adding +0.0 leaves a float32 sum that is not -0.0
+// unchanged, and sums of values that are never -0.0 are never -0.0, so the
+// padded sums equal the CSR-order sums exactly and the inner loop needs no
+// predicates.  DUP (64-byte rows): the block of x is stored with a 128-byte
+// pitch and each row twice, at bytes [0,64) and [64,128); row groups of odd
+// index read the second copy, so the two row groups of a half-warp always
+// use opposite halves of the 32 banks.
+template <typename TX, typename TV, int VEC, int LPR, bool MIS, bool DUP>
 __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int RPW = 32 / LPR;
   const int it = blockIdx.x;
   const Item item = a.g.items[it];
   const int g = item.g;
@@ -250,11 +256,11 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   const int BW = a.Bw;
   const int32_t off = a.g.node_off[g];
   const int32_t ng = a.g.node_off[g + 1] - off;
-  const int rowb = B * (int)sizeof(TX);           // bytes of one node's x
+  const int rowb = B * (int)sizeof(TX);  // bytes of one node's x
   const int pitch = DUP ? 128 : rowb;
-  const size_t xbytes = ((size_t)ng * pitch + 15) & ~(size_t)15;
+  const size_t xbytes = ((size_t)(ng + 1) * pitch + 15) & ~(size_t)15;
   uint32_t* sZ = reinterpret_cast<uint32_t*>(smem + xbytes);
-  const size_t zbytes = MIS ? (((size_t)ng * BW * 4 + 15) & ~(size_t)15) : 0;
+  const size_t zbytes = MIS ? (((size_t)(ng + 1) * BW * 4 + 15) & ~(size_t)15) : 0;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem + xbytes + zbytes);
 
   const TX* __restrict__ Xc = static_cast<const TX*>((t & 1) ? a.X1 : a.X0);
@@ -263,7 +269,8 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   uint32_t* __restrict__ Zn = (t & 1) ? a.ZX0 : a.ZX1;
   TV* __restrict__ V = static_cast<TV*>(a.V);
 
-  // stage the member graph's x block (16-byte copies) and rounding words
+  // stage the member graph's x block (16-byte copies), the zero dummy row,
+  // and the rounding words
   {
     const int4* src = reinterpret_cast<const int4*>(Xc + (int64_t)off * B);
     const int per = rowb / 16;  // 16-byte pieces per node
@@ -275,19 +282,20 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
       *reinterpret_cast<int4*>(d) = vv;
       if (DUP) *reinterpret_cast<int4*>(d + 64) = vv;
     }
+    for (int i = threadIdx.x; i < pitch / 16; i += blockDim.x)
+      *reinterpret_cast<int4*>(smem + (size_t)ng * pitch + i * 16) = make_int4(0, 0, 0, 0);
     if (MIS) {
       const uint32_t* zs = Zc + (int64_t)off * BW;
       for (int i = threadIdx.x; i < ng * BW; i += blockDim.x) sZ[i] = zs[i];
+      for (int i = threadIdx.x; i < BW; i += blockDim.x) sZ[ng * BW + i] = 0u;
     }
     for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) s_cnt[i] = 0ull;
   }
   __syncthreads();
 
-  const int lpr = B / VEC;
-  const int rpw = 32 / lpr;
   const int lane = threadIdx.x & 31;
-  const int sub = lane / lpr;
-  const int l = lane - sub * lpr;
+  const int sub = lane / LPR;
+  const int l = lane - sub * LPR;
   const int b0 = l * VEC;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -297,8 +305,8 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   const int32_t* __restrict__ rp = a.g.row_ptr;
   const int32_t* __restrict__ col = a.g.col;
   const int8_t* __restrict__ wts = a.g.w;
-  const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;  // lanes sharing one output word
-  const unsigned rmask = lpr == 32 ? 0xffffffffu : (((1u << lpr) - 1u) << (sub * lpr));
+  constexpr int K = (LPR < 32 / VEC) ? LPR : 32 / VEC;  // lanes sharing one output word
+  const unsigned rmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (sub * LPR));
   const unsigned char* sXl = smem + (DUP ? (sub & 1) * 64 : 0) + l * (VEC * (int)sizeof(TX));
 
   bool stepping[VEC];
@@ -308,12 +316,10 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
 #pragma unroll
   for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
 
-  // rows of this item, RPW per warp per pass; the warp loops while any of
-  // its row groups has a row
-  for (int vb = item.v0 + warp * rpw; vb < item.v1; vb += nwarps * rpw) {
+  for (int vb = item.v0 + warp * RPW; vb < item.v1; vb += nwarps * RPW) {
     const int v = vb + sub;
     const bool has = v < item.v1;
-    const int vl = has ? v - off : 0;
+    const int vl = has ? v - off : ng;
     const int64_t base = (int64_t)(has ? v : item.v0) * B + b0;
     const Pack<TX, VEC> xv = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)vl * pitch);
     Pack<TV, VEC> vv{};
@@ -324,53 +330,45 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
     const int rs = has ? rp[v] : 0, re = has ? rp[v + 1] : 0;
-    const int nch = (re - rs + lpr - 1) / lpr;
-    const int nch_w = __reduce_max_sync(0xffffffffu, nch);
-    int wsum = 0;
+    const int nch_w = __reduce_max_sync(0xffffffffu, (re - rs + LPR - 1) / LPR);
+    int wsum = weighted ? 0 : re - rs;
     // column indices of four chunks are loaded before any of them is used
     for (int ch0 = 0; ch0 < nch_w; ch0 += 4) {
       int myu[4], myw[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int j = rs + (ch0 + c) * lpr + l;
+        const int j = rs + (ch0 + c) * LPR + l;
         const bool jin = j < re;
-        myu[c] = jin ? __ldcs(col + j) - off : 0;
-        myw[c] = (weighted && jin) ? (int)wts[j] : 1;
+        myu[c] = jin ? __ldcs(col + j) - off : ng;
+        myw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
       }
       if (MIS) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (rs + (ch0 + c) * lpr + l < re) {
-            for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu[c] * BW + w];
-          }
-        }
+        for (int c = 0; c < 4; ++c)
+          for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu[c] * BW + w];
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int cb = rs + (ch0 + c) * lpr;
-        const int cnt = max(0, min(lpr, re - cb));
-        const int cnt_w = __reduce_max_sync(0xffffffffu, cnt);
-        if (cnt_w == 0) break;
-        for (int k = 0; k < cnt_w; k += 4) {
-          int u[4], w[4];
-          Pack<TX, VEC> p[4];
+        if (ch0 + c >= nch_w) break;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            u[q] = __shfl_sync(0xffffffffu, myu[c], k + q, lpr);
-            w[q] = weighted ? __shfl_sync(0xffffffffu, myw[c], k + q, lpr) : 1;
-          }
+        for (int k = 0; k < LPR; ++k) {
+          const int u = __shfl_sync(0xffffffffu, myu[c], k, LPR);
+          const Pack<TX, VEC> p = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)u * pitch);
+          if (weighted) {
+            const int w = __shfl_sync(0xffffffffu, myw[c], k, LPR);
+            wsum += w;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) p[q] = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)u[q] * pitch);
+            for (int e = 0; e < VEC; ++e) {
+              const float f = to_f(p.e[e]);
+              acc[e] = w >= 0 ? acc[e] + f : acc[e] - f;
+              pos[e] += (f > thr) ? w : 0;
+            }
+          } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (k + q < cnt) {
-              wsum += w[q];
-#pragma unroll
-              for (int e = 0; e < VEC; ++e) {
-                const float f = to_f(p[q].e[e]);
-                acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
-                if (!MIS) pos[e] += (f > thr) ? w[q] : 0;
-              }
+            for (int e = 0; e < VEC; ++e) {
+              const float f = to_f(p.e[e]);
+              acc[e] = acc[e] + f;
+              if (!MIS) pos[e] += (f > thr);
             }
           }
         }
@@ -378,7 +376,7 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     }
     if (MIS) {
       for (int w = 0; w < BW; ++w)
-        for (int o = 1; o < lpr; o <<= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
+        for (int o = 1; o < LPR; o <<= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         const int bb = b0 + e;
@@ -409,46 +407,44 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
       st_pack<TV, VEC>(V + base, vo);
     }
     unsigned word = zbits << (b0 & 31);
+#pragma unroll
     for (int o = 1; o < K; o <<= 1) word |= __shfl_xor_sync(rmask, word, o);
     if (has && (l % K) == 0) Zn[(int64_t)v * BW + (b0 >> 5)] = word;
   }
   flush_step_counters<VEC>(a, s_cnt, g, it, b0, c0, c1, c2, stepping);
 }
 
-// lanes hold 8 bytes of x (or B/32 elements if more), so VEC = max(8/sx, B/32)
-static int smem_vec(int B, int x_dtype) {
-  const int sx = x_dtype == DT_F32 ? 4 : 2;
-  const int v8 = 8 / sx;
-  return B / 32 > v8 ? B / 32 : v8;
-}
-
 size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng) {
   const size_t sx = x_dtype == DT_F32 ? 4 : 2;
   const size_t rowb = (size_t)B * sx;
   const size_t pitch = rowb == 64 ? 128 : rowb;
-  const size_t xb = ((size_t)max_ng * pitch + 15) & ~(size_t)15;
-  const size_t zb = problem == PROB_MIS ? (((size_t)max_ng * ((B + 31) / 32) * 4 + 15) & ~(size_t)15) : 0;
+  const size_t xb = ((size_t)(max_ng + 1) * pitch + 15) & ~(size_t)15;
+  const size_t zb = problem == PROB_MIS ? (((size_t)(max_ng + 1) * ((B + 31) / 32) * 4 + 15) & ~(size_t)15) : 0;
   return xb + zb + 3 * (size_t)B * 8;
 }
 
-template <typename TX, typename TV, int VEC, bool MIS>
-static cudaError_t launch_s(size_t smem, bool dup, const StepArgs& a, int grid, cudaStream_t s) {
-  if (dup) {
-    cudaFuncSetAttribute(k_step_s<TX, TV, VEC, MIS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_step_s<TX, TV, VEC, MIS, true><<<grid, 512, smem, s>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_step_s<TX, TV, VEC, MIS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_step_s<TX, TV, VEC, MIS, false><<<grid, 512, smem, s>>>(a);
-  }
+template <typename TX, typename TV, int VEC, int LPR, bool MIS, bool DUP>
+static cudaError_t launch_s(size_t smem, const StepArgs& a, int grid, cudaStream_t s) {
+  cudaFuncSetAttribute(k_step_s<TX, TV, VEC, LPR, MIS, DUP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_step_s<TX, TV, VEC, LPR, MIS, DUP><<<grid, 512, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+// lanes hold 8 bytes of x, or 16 when B/32 elements need more:
+// 2-byte x: B=32 -> (VEC 4, LPR 8, DUP), B=64 -> (4, 16), B=128 -> (4, 32);
+// 4-byte x: B=32 -> (2, 16), B=64 -> (2, 32), B=128 -> (4, 32)
 template <typename TX, typename TV>
 static cudaError_t launch_smem(int B, size_t smem, bool mis, const StepArgs& a, int grid, cudaStream_t s) {
-  const int vec = smem_vec(B, sizeof(TX) == 4 ? DT_F32 : DT_BF16);
-  const bool dup = B * (int)sizeof(TX) == 64;
-  if (vec == 2) return mis ? launch_s<TX, TV, 2, true>(smem, dup, a, grid, s) : launch_s<TX, TV, 2, false>(smem, dup, a, grid, s);
-  if (vec == 4) return mis ? launch_s<TX, TV, 4, true>(smem, dup, a, grid, s) : launch_s<TX, TV, 4, false>(smem, dup, a, grid, s);
+  constexpr bool two = sizeof(TX) == 2;
+  if (mis) {
+    if (B == 32) return two ? launch_s<TX, TV, 4, 8, true, true>(smem, a, grid, s) : launch_s<TX, TV, 2, 16, true, false>(smem, a, grid, s);
+    if (B == 64) return two ? launch_s<TX, TV, 4, 16, true, false>(smem, a, grid, s) : launch_s<TX, TV, 2, 32, true, false>(smem, a, grid, s);
+    if (B == 128) return launch_s<TX, TV, 4, 32, true, false>(smem, a, grid, s);
+  } else {
+    if (B == 32) return two ? launch_s<TX, TV, 4, 8, false, true>(smem, a, grid, s) : launch_s<TX, TV, 2, 16, false, false>(smem, a, grid, s);
+    if (B == 64) return two ? launch_s<TX, TV, 4, 16, false, false>(smem, a, grid, s) : launch_s<TX, TV, 2, 32, false, false>(smem, a, grid, s);
+    if (B == 128) return launch_s<TX, TV, 4, 32, false, false>(smem, a, grid, s);
+  }
   return cudaErrorInvalidValue;
 }
 
