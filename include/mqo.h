@@ -250,9 +250,11 @@ MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
 
 /*
  * Execution plan chosen at creation (host, any pointer may be NULL):
- * *step_kernel = 1 if the fused step stages each member graph's block of x
- * in shared memory (every member graph fits), 0 for the global-memory
- * kernel; *smem_bytes = its dynamic shared memory per CTA; *items = CTAs
+ * *step_kernel bit 0 = the fused step stages each member graph's block of x
+ * in shared memory (every member graph fits; else the global-memory
+ * kernel), bit 1 = the discrete passes run fused, one CTA per member graph
+ * (else three node-parallel launches); *smem_bytes = the step kernel's
+ * dynamic shared memory per CTA; *items = CTAs
  * per step (node ranges of at most 256 nodes); *replicas = counter
  * replicas per trajectory.
  */

@@ -271,7 +271,8 @@ class Solver:
         """Execution plan: step kernel (1 shared-memory staged, 0 global), smem bytes, items, counter replicas."""
         k, sm, it, r = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
         _check(lib().mqo_solver_info(self.handle, C.byref(k), C.byref(sm), C.byref(it), C.byref(r)))
-        return {"step_kernel": "smem" if k.value else "global", "smem_bytes": sm.value, "items": it.value,
+        return {"step_kernel": "smem" if k.value & 1 else "global",
+                "discrete_kernel": "graph" if k.value & 2 else "pairs", "smem_bytes": sm.value, "items": it.value,
                 "replicas": r.value}
 
     def traj_state(self):

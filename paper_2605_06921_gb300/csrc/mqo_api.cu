@@ -36,6 +36,7 @@ mqo_status fail(mqo_status st, const char* fmt, ...) {
 constexpr int kChunkNodes = 256;  // nodes per item
 constexpr int kSplit = 512;       // row length above which the f_B kernels chunk a row
 constexpr size_t kStepSmemLimit = 110 * 1024;  // shared-memory step kernel if the graph block fits
+constexpr size_t kDiscSmemLimit = 96 * 1024;   // fused discrete kernel if the graph's bit words fit
 
 }  // namespace
 
@@ -93,6 +94,7 @@ struct mqo_solver_s {
   bool poisoned = false;
   int grid = 1;
   size_t step_smem = 0;  // > 0: shared-memory step kernel with this much dynamic smem
+  size_t disc_smem = 0;  // > 0: fused per-graph discrete kernel with this much dynamic smem
   int64_t host_tick = 0;
   Counters* d_cnt_plain = nullptr;
   Counters* d_eval = nullptr;
@@ -321,8 +323,12 @@ cudaError_t enqueue_tick(mqo_solver s) {
   if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
   if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
   if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work)) != cudaSuccess) return e;
-  for (int pass = 0; pass < 3; ++pass)
-    if ((e = launch_disc(S, pass, s->work)) != cudaSuccess) return e;
+  if (s->disc_smem > 0) {
+    if ((e = launch_disc_graph(S, s->disc_smem, s->work)) != cudaSuccess) return e;
+  } else {
+    for (int pass = 0; pass < 3; ++pass)
+      if ((e = launch_disc(S, pass, s->work)) != cudaSuccess) return e;
+  }
   return launch_tick_end(S, s->work);
 }
 
@@ -331,8 +337,12 @@ cudaError_t enqueue_ls_tick(mqo_solver s, int mode) {
   const SolverDev& S = s->S;
   if ((e = launch_ctrl(S, mode, nullptr, s->work)) != cudaSuccess) return e;
   if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
-  for (int pass = 0; pass < 3; ++pass)
-    if ((e = launch_disc(S, pass, s->work)) != cudaSuccess) return e;
+  if (s->disc_smem > 0) {
+    if ((e = launch_disc_graph(S, s->disc_smem, s->work)) != cudaSuccess) return e;
+  } else {
+    for (int pass = 0; pass < 3; ++pass)
+      if ((e = launch_disc(S, pass, s->work)) != cudaSuccess) return e;
+  }
   return launch_tick_end(S, s->work);
 }
 
@@ -505,6 +515,12 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     const char* force = getenv("MQO_STEP_KERNEL");
     const bool generic = force && strcmp(force, "generic") == 0;
     s->step_smem = (!generic && B >= 32 && need <= kStepSmemLimit) ? need : 0;
+    // MQO_DISC_KERNEL=pairs selects the three node-parallel discrete passes
+    // even when every member graph's bit words fit in shared memory
+    const char* dforce = getenv("MQO_DISC_KERNEL");
+    const bool pairs = dforce && strcmp(dforce, "pairs") == 0;
+    const size_t dneed = disc_graph_smem_bytes(B, max_ng);
+    s->disc_smem = (!pairs && B >= 32 && dneed <= kDiscSmemLimit) ? dneed : 0;
   }
   const size_t TR = (size_t)T * S.R;
   if ((st = dalloc(&S.st, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
@@ -612,7 +628,11 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t
       if (ek == cudaSuccess) ek = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
       if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       for (int pass = 0; pass < 3 && ek == cudaSuccess; ++pass) {
-        ek = launch_disc(S, pass, s->work);
+        if (s->disc_smem > 0) {
+          if (pass == 0) ek = launch_disc_graph(S, s->disc_smem, s->work);  // all three passes fused
+        } else {
+          ek = launch_disc(S, pass, s->work);
+        }
         if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       }
       if (ek == cudaSuccess) ek = launch_tick_end(S, s->work);
@@ -771,7 +791,7 @@ mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits) {
 mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_bytes, int32_t* items,
                            int32_t* replicas) {
   if (!s) return fail(MQO_EINVAL, "null solver");
-  if (step_kernel) *step_kernel = s->step_smem > 0 ? 1 : 0;
+  if (step_kernel) *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0);
   if (smem_bytes) *smem_bytes = (int64_t)s->step_smem;
   if (items) *items = s->S.g.num_items;
   if (replicas) *replicas = s->S.R;

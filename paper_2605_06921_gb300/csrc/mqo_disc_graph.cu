@@ -1,0 +1,305 @@
+// mqo_disc_graph.cu -- the discrete passes of a tick (repair and local
+// search rounds, then the counts of the work set) fused into one kernel for
+// member graphs that fit in shared memory: one CTA per member graph stages
+// the graph's bit words (work set, tight / positive-gain bits, free bits,
+// drop bits) in shared memory and runs pass A (decide / propose), pass B
+// (commit) and pass C (count) with block barriers in between, then writes
+// the words back.  Same rounds and results as the three k_disc launches
+// (see mqo_tick.cu): repair = Def. 2.1 feasibility + maximality; rounds of
+// (1,2)-swaps (Def. 2.3), 1-flips (Def. 2.4) and 2-flips (Def. 2.5).
+//
+// Mapping: B >= 32 (Bw = B/32 words per node).  Warp w always handles word
+// w % Bw of its nodes, so lane l always owns trajectory (w % Bw)*32 + l and
+// keeps its counters in registers.  Whole-word set logic (ORs over smaller
+// neighbours, once/twice counts) is computed by the warp's 32 lanes
+// together from shared memory.
+#include "mqo_dev.cuh"
+#include "mqo_host.h"
+
+namespace mqo {
+
+namespace {
+
+constexpr int kDgThreads = 512;
+
+// OR over the neighbours u of v (only u < v if `less`) of word wk of `words`
+// (shared memory, local node ids), by the 32 lanes of a warp together
+__device__ __forceinline__ uint32_t warp_nb_or(const uint32_t* words, const int32_t* col, int32_t rs, int32_t re,
+                                               int32_t off, int Bw, int wk, int vl, bool less) {
+  uint32_t r = 0u;
+  const int lane = threadIdx.x & 31;
+  for (int32_t j = rs + lane; j < re; j += 32) {
+    const int32_t u = col[j] - off;
+    if (less && u >= vl) break;
+    r |= words[u * Bw + wk];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r |= __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+__device__ __forceinline__ bool sbit(const uint32_t* words, int u, int Bw, int b) {
+  return (words[u * Bw + (b >> 5)] >> (b & 31)) & 1u;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int g = blockIdx.x;
+  const int64_t t = *S.tick;
+  if (S.any[1] != (int32_t)(t + 1)) return;
+  const int G = S.g.num_graphs;
+  if (S.gflag[G + g] != (int32_t)(t + 1)) return;
+  const int B = S.B, Bw = S.Bw;
+  const bool mis = S.p.problem == PROB_MIS;
+  const int32_t off = S.g.node_off[g];
+  const int32_t ng = S.g.node_off[g + 1] - off;
+  const int32_t* rp = S.g.row_ptr;
+  const int32_t* col = S.g.col;
+  const int8_t* wts = S.g.w;
+  const int nw = ng * Bw;
+  uint32_t* sW = reinterpret_cast<uint32_t*>(smem);  // work set
+  uint32_t* sA = sW + nw;                            // tight / positive gain
+  uint32_t* sF = sA + nw;                            // free
+  uint32_t* sD = sF + nw;                            // drop decisions
+  int* s_rnd = reinterpret_cast<int*>(sD + nw);      // round of each trajectory
+  unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_rnd + ((B + 1) & ~1));
+
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+    const int64_t gi = (int64_t)off * Bw + i;
+    sW[i] = S.Zwork[gi];
+    sA[i] = S.Zaux[gi];
+    sF[i] = S.Zfree[gi];
+    sD[i] = 0u;
+  }
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_rnd[i] = S.rnd[(int64_t)g * B + i];
+  for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;  // a multiple of Bw (Bw <= 4)
+  const int wk = warp % Bw;
+  const int b = wk * 32 + lane;
+  const int round = s_rnd[b];
+  const uint32_t bit = 1u << lane;
+  const int vstep = nwarps / Bw;
+  long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+
+  // ---------------- pass A: decisions on the snapshot
+  for (int vl = warp / Bw; vl < ng; vl += vstep) {
+    const int64_t v = off + vl;
+    const int32_t rs = rp[v], re = rp[v + 1];
+    const int64_t e = v * B + b;
+    const bool zv = sbit(sW, vl, Bw, b);
+    bool dropv = false, addv = false, flipv = false;
+    if (__any_sync(0xffffffffu, round == RD_DROP)) {
+      const uint32_t o = warp_nb_or(sW, col, rs, re, off, Bw, wk, vl, true);
+      dropv = round == RD_DROP && zv && (o & bit);
+    }
+    if (__any_sync(0xffffffffu, round == RD_COMPLETE)) {
+      const uint32_t o = warp_nb_or(sF, col, rs, re, off, Bw, wk, vl, true);
+      addv = round == RD_COMPLETE && sbit(sF, vl, Bw, b) && !(o & bit);
+    }
+    if (__any_sync(0xffffffffu, round == RD_FLIP1)) {
+      const uint32_t o = warp_nb_or(sA, col, rs, re, off, Bw, wk, vl, true);
+      flipv = round == RD_FLIP1 && sbit(sA, vl, Bw, b) && !(o & bit);
+    }
+    const unsigned md = __ballot_sync(0xffffffffu, dropv);
+    const unsigned mc = __ballot_sync(0xffffffffu, addv || flipv);
+    if (lane == 0) {
+      sD[vl * Bw + wk] = md;
+      if (mc) sW[vl * Bw + wk] ^= mc;  // complete sets clear bits, flip1 toggles
+    }
+    acc3 += dropv + addv + flipv;
+    if (round == RD_SWAP) {
+      int32_t fa = -1, fb = -1;
+      if (zv) {
+        for (int32_t i = rs; i < re && fa < 0; ++i) {
+          const int32_t a = col[i];
+          if (!sbit(sA, a - off, Bw, b)) continue;
+          for (int32_t j = i + 1; j < re; ++j) {
+            const int32_t cc = col[j];
+            if (!sbit(sA, cc - off, Bw, b)) continue;
+            if (!sorted_contains(col, rp[a], rp[a + 1], cc)) {
+              fa = a;
+              fb = cc;
+              break;
+            }
+          }
+        }
+      }
+      S.pa[e] = fa;
+      S.pb[e] = fb;
+      if (fa >= 0) {
+        S.owner[(int64_t)fa * B + b] = (int32_t)v;
+        S.owner[(int64_t)fb * B + b] = (int32_t)v;
+      }
+    }
+    if (round == RD_FLIP2) {
+      int32_t fb = -1;
+      const int32_t ga = S.gain[e];
+      for (int32_t j = rs; j < re; ++j) {
+        const int32_t u = col[j];
+        if (u <= v) continue;
+        if (sbit(sW, u - off, Bw, b) == zv) continue;
+        const int w = wts ? (int)wts[j] : 1;
+        if (ga + S.gain[(int64_t)u * B + b] + 2 * w > 0) {
+          fb = u;
+          break;
+        }
+      }
+      S.pb[e] = fb;
+      if (fb >= 0) {
+        atomicMin(&S.owner[e], (int32_t)v);
+        atomicMin(&S.owner[(int64_t)fb * B + b], (int32_t)v);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------- pass B: commits
+  for (int vl = warp / Bw; vl < ng; vl += vstep) {
+    const int64_t v = off + vl;
+    const int64_t e = v * B + b;
+    const unsigned md = sD[vl * Bw + wk];
+    if (lane == 0 && md) atomicAnd(&sW[vl * Bw + wk], ~md);
+    if (round == RD_SWAP) {
+      const int32_t fa = S.pa[e];
+      if (fa >= 0) {
+        const int32_t fb = S.pb[e];
+        bool ok = true;
+        const int32_t ends[2] = {fa, fb};
+        for (int k = 0; k < 2 && ok; ++k) {
+          const int32_t x = ends[k];
+          for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+            if (S.owner[(int64_t)col[j] * B + b] < (int32_t)v) {
+              ok = false;
+              break;
+            }
+          }
+        }
+        if (ok) {
+          atomicAnd(&sW[vl * Bw + wk], ~bit);
+          atomicOr(&sW[(fa - off) * Bw + wk], bit);
+          atomicOr(&sW[(fb - off) * Bw + wk], bit);
+          acc3 += 1;
+        }
+      }
+    }
+    if (round == RD_FLIP2) {
+      const int32_t fb = S.pb[e];
+      if (fb >= 0) {
+        bool ok = S.owner[e] == (int32_t)v && S.owner[(int64_t)fb * B + b] == (int32_t)v;
+        const int32_t ends[2] = {(int32_t)v, fb};
+        for (int k = 0; k < 2 && ok; ++k) {
+          const int32_t x = ends[k];
+          for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+            const int32_t y = col[j];
+            if (y == (int32_t)v || y == fb) continue;
+            if (S.owner[(int64_t)y * B + b] < (int32_t)v) {
+              ok = false;
+              break;
+            }
+          }
+        }
+        if (ok) {
+          atomicXor(&sW[vl * Bw + wk], bit);
+          atomicXor(&sW[(fb - off) * Bw + wk], bit);
+          acc3 += 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------- pass C: counts of the (new) work set
+  const bool act = round != RD_NONE;
+  for (int vl = warp / Bw; vl < ng; vl += vstep) {
+    const int64_t v = off + vl;
+    const int32_t rs = rp[v], re = rp[v + 1];
+    const int64_t e = v * B + b;
+    const bool zv = sbit(sW, vl, Bw, b);
+    bool aux = false, fr = false;
+    if (act) S.owner[e] = 0x7fffffff;
+    if (mis) {
+      uint32_t once = 0u, twice = 0u;
+      for (int32_t j = rs + lane; j < re; j += 32) {
+        const uint32_t w = sW[(col[j] - off) * Bw + wk];
+        twice |= once & w;
+        once |= w;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, once, o);
+        const uint32_t t2 = __shfl_xor_sync(0xffffffffu, twice, o);
+        twice = twice | t2 | (once & o2);
+        once |= o2;
+      }
+      if (act) {
+        const bool one = (once & bit) != 0, two = (twice & bit) != 0;
+        acc0 += zv;
+        acc1 += zv && one;
+        fr = !zv && !one;
+        acc2 += fr;
+        aux = !zv && one && !two;
+      }
+    } else if (act) {
+      int P = 0, W = 0;
+      for (int32_t j = rs; j < re; ++j) {
+        const int w = wts ? (int)wts[j] : 1;
+        W += w;
+        if (sbit(sW, col[j] - off, Bw, b)) P += w;
+      }
+      const int as = 2 * P - W;
+      acc0 += zv ? (W - P) : P;
+      acc1 += !(zv ? (as <= -1) : (as >= 0));
+      const int gn = zv ? as : -as;
+      acc2 += gn > 0;
+      S.gain[e] = gn;
+      aux = gn > 0;
+    }
+    const unsigned ma = __ballot_sync(0xffffffffu, act);
+    const unsigned mx = __ballot_sync(0xffffffffu, aux);
+    const unsigned mf = __ballot_sync(0xffffffffu, fr);
+    if (lane == 0 && ma) {
+      sA[vl * Bw + wk] = (sA[vl * Bw + wk] & ~ma) | (mx & ma);
+      if (mis) sF[vl * Bw + wk] = (sF[vl * Bw + wk] & ~ma) | (mf & ma);
+    }
+  }
+  if (acc0) atomicAdd(&s_cnt[4 * b + 0], (unsigned long long)acc0);
+  if (acc1) atomicAdd(&s_cnt[4 * b + 1], (unsigned long long)acc1);
+  if (acc2) atomicAdd(&s_cnt[4 * b + 2], (unsigned long long)acc2);
+  if (acc3) atomicAdd(&s_cnt[4 * b + 3], (unsigned long long)acc3);
+  __syncthreads();
+
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+    const int64_t gi = (int64_t)off * Bw + i;
+    S.Zwork[gi] = sW[i];
+    S.Zaux[gi] = sA[i];
+    S.Zfree[gi] = sF[i];
+  }
+  for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) {
+    const unsigned long long val = s_cnt[i];
+    if (val) {
+      Counters* c = S.cnt + ((int64_t)g * B + i / 4) * S.R;  // replica 0
+      const int k = i & 3;
+      unsigned long long* p = k == 0 ? &c->value : k == 1 ? &c->a : k == 2 ? &c->b : &c->commits;
+      atomicAdd(p, val);
+    }
+  }
+}
+
+size_t disc_graph_smem_bytes(int B, int max_ng) {
+  const size_t nw = (size_t)max_ng * ((B + 31) / 32);
+  return 4 * nw * 4 + (size_t)((B + 1) & ~1) * 4 + 4 * (size_t)B * 8;
+}
+
+cudaError_t launch_disc_graph(const SolverDev& S, size_t smem, cudaStream_t stream) {
+  cudaFuncSetAttribute(k_disc_graph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_disc_graph<<<S.g.num_graphs, kDgThreads, smem, stream>>>(S);
+  return cudaGetLastError();
+}
+
+}  // namespace mqo

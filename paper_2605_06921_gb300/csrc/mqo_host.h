@@ -19,6 +19,8 @@ size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng);
 cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream);
 cudaError_t launch_apply(const SolverDev& S, cudaStream_t stream);
 cudaError_t launch_disc(const SolverDev& S, int pass, cudaStream_t stream);
+size_t disc_graph_smem_bytes(int B, int max_ng);
+cudaError_t launch_disc_graph(const SolverDev& S, size_t smem, cudaStream_t stream);
 cudaError_t launch_tick_end(const SolverDev& S, cudaStream_t stream);
 cudaError_t launch_round_bits(const SolverDev& S, uint32_t* z, cudaStream_t stream);
 cudaError_t launch_eval(const SolverDev& S, const uint32_t* z, Counters* out, cudaStream_t stream);

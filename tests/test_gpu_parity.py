@@ -132,9 +132,11 @@ def test_plain_steps_batch_sizes_mis(mq, B):
 @pytest.mark.parametrize("problem", [0, 1])
 @pytest.mark.parametrize("B,xd", [(32, 0), (32, 1), (64, 0), (128, 1)])
 def test_generic_step_kernel_on_small_graphs(mq, monkeypatch, problem, B, xd):
-    """the global-memory step kernel (used for large graphs) on graphs that
-    would otherwise take the shared-memory kernel"""
+    """the global-memory step kernel and the node-parallel discrete passes
+    (used for large graphs) on graphs that would otherwise take the
+    shared-memory kernels"""
     monkeypatch.setenv("MQO_STEP_KERNEL", "generic")
+    monkeypatch.setenv("MQO_DISC_KERNEL", "pairs")
     p = mq.params(problem=problem, batch=B, x_dtype=xd, alpha=0.8 if problem == 0 else 0.05, momentum=0.5, seed=B)
     _plain_steps(mq, small_batch(2, seed=B + 1), p, 8)
     G = small_batch(2, 30, 60, 0.15, seed=B)
