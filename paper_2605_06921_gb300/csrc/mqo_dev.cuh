@@ -248,6 +248,56 @@ __device__ __forceinline__ void st_pack(T* p, const Pack<T, VEC>& v) {
   *reinterpret_cast<Pack<T, VEC>*>(p) = v;
 }
 
+// VEC elements of T at p (aligned to VEC*sizeof(T)) as floats, read with one
+// vector load.  bfloat16 -> float is exact: the 16 bits become the high half
+// of the float's bits; binary16 goes through the half2 conversion.
+template <typename T, int VEC>
+__device__ __forceinline__ void load_unpack(const unsigned char* p, float* f);
+template <>
+__device__ __forceinline__ void load_unpack<__nv_bfloat16, 4>(const unsigned char* p, float* f) {
+  const uint2 r = *reinterpret_cast<const uint2*>(p);
+  f[0] = __uint_as_float(r.x << 16);
+  f[1] = __uint_as_float(r.x & 0xffff0000u);
+  f[2] = __uint_as_float(r.y << 16);
+  f[3] = __uint_as_float(r.y & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void load_unpack<__half, 4>(const unsigned char* p, float* f) {
+  const uint2 r = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+  f[0] = a.x;
+  f[1] = a.y;
+  f[2] = b.x;
+  f[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void load_unpack<__nv_bfloat16, 2>(const unsigned char* p, float* f) {
+  const uint32_t r = *reinterpret_cast<const uint32_t*>(p);
+  f[0] = __uint_as_float(r << 16);
+  f[1] = __uint_as_float(r & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void load_unpack<__half, 2>(const unsigned char* p, float* f) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
+  f[0] = a.x;
+  f[1] = a.y;
+}
+template <>
+__device__ __forceinline__ void load_unpack<float, 2>(const unsigned char* p, float* f) {
+  const float2 r = *reinterpret_cast<const float2*>(p);
+  f[0] = r.x;
+  f[1] = r.y;
+}
+template <>
+__device__ __forceinline__ void load_unpack<float, 4>(const unsigned char* p, float* f) {
+  const float4 r = *reinterpret_cast<const float4*>(p);
+  f[0] = r.x;
+  f[1] = r.y;
+  f[2] = r.z;
+  f[3] = r.w;
+}
+
 __device__ __forceinline__ float clamp_box(float v, float lo, float hi) {
   if (v < lo) return lo;
   if (v > hi) return hi;

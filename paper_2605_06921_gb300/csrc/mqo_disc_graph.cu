@@ -22,24 +22,76 @@ namespace {
 
 constexpr int kDgThreads = 512;
 
-// OR over the neighbours u of v (only u < v if `less`) of word wk of `words`
-// (shared memory, local node ids), by the 32 lanes of a warp together
-__device__ __forceinline__ uint32_t warp_nb_or(const uint32_t* words, const int32_t* col, int32_t rs, int32_t re,
-                                               int32_t off, int Bw, int wk, int vl, bool less) {
-  uint32_t r = 0u;
+__device__ __forceinline__ bool sbit(const uint32_t* words, int u, int Bw, int b) {
+  return (words[u * Bw + (b >> 5)] >> (b & 31)) & 1u;
+}
+
+// A node's neighbour list held in registers: lane l holds entries
+// rs + l + 32k (k < kNb) as local ids, -1 past the end.  The loads of a list
+// are independent, so one list costs one memory latency; longer rows keep
+// their tail (entries past rs + 32 kNb) in memory.
+constexpr int kNb = 5;
+
+struct NbList {
+  int32_t u[kNb];
+  int32_t rs, re;
+};
+
+__device__ __forceinline__ void nb_load(NbList& L, const int32_t* s_rp, const int32_t* col, int32_t off, int vl) {
   const int lane = threadIdx.x & 31;
-  for (int32_t j = rs + lane; j < re; j += 32) {
+  L.rs = s_rp[vl];
+  L.re = s_rp[vl + 1];
+#pragma unroll
+  for (int k = 0; k < kNb; ++k) {
+    const int32_t j = L.rs + lane + 32 * k;
+    L.u[k] = j < L.re ? __ldcs(col + j) - off : -1;
+  }
+}
+
+// OR over the list (only u < vl if `less`) of word wk of `words`
+__device__ __forceinline__ uint32_t nb_or(const NbList& L, const uint32_t* words, const int32_t* col, int32_t off,
+                                          int Bw, int wk, int vl, bool less) {
+  const int lane = threadIdx.x & 31;
+  uint32_t r = 0u;
+#pragma unroll
+  for (int k = 0; k < kNb; ++k) {
+    const int32_t u = L.u[k];
+    if (u >= 0 && (!less || u < vl)) r |= words[u * Bw + wk];
+  }
+  for (int32_t j = L.rs + 32 * kNb + lane; j < L.re; j += 32) {
     const int32_t u = col[j] - off;
-    if (less && u >= vl) break;
-    r |= words[u * Bw + wk];
+    if (!less || u < vl) r |= words[u * Bw + wk];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r |= __shfl_xor_sync(0xffffffffu, r, o);
   return r;
 }
 
-__device__ __forceinline__ bool sbit(const uint32_t* words, int u, int Bw, int b) {
-  return (words[u * Bw + (b >> 5)] >> (b & 31)) & 1u;
+// bits set in at least one / at least two neighbours' word wk
+__device__ __forceinline__ void nb_once_twice(const NbList& L, const uint32_t* words, const int32_t* col,
+                                              int32_t off, int Bw, int wk, uint32_t& once, uint32_t& twice) {
+  const int lane = threadIdx.x & 31;
+  once = 0u;
+  twice = 0u;
+#pragma unroll
+  for (int k = 0; k < kNb; ++k) {
+    const int32_t u = L.u[k];
+    const uint32_t w = u >= 0 ? words[u * Bw + wk] : 0u;
+    twice |= once & w;
+    once |= w;
+  }
+  for (int32_t j = L.rs + 32 * kNb + lane; j < L.re; j += 32) {
+    const uint32_t w = words[(col[j] - off) * Bw + wk];
+    twice |= once & w;
+    once |= w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t o2 = __shfl_xor_sync(0xffffffffu, once, o);
+    const uint32_t t2 = __shfl_xor_sync(0xffffffffu, twice, o);
+    twice = twice | t2 | (once & o2);
+    once |= o2;
+  }
 }
 
 }  // namespace
@@ -65,6 +117,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   uint32_t* sD = sF + nw;                            // drop decisions
   int* s_rnd = reinterpret_cast<int*>(sD + nw);      // round of each trajectory
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_rnd + ((B + 1) & ~1));
+  int32_t* s_rp = reinterpret_cast<int32_t*>(s_cnt + 4 * B);  // row pointers of the graph
 
   for (int i = threadIdx.x; i < nw; i += blockDim.x) {
     const int64_t gi = (int64_t)off * Bw + i;
@@ -75,6 +128,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   }
   for (int i = threadIdx.x; i < B; i += blockDim.x) s_rnd[i] = S.rnd[(int64_t)g * B + i];
   for (int i = threadIdx.x; i < 4 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  for (int i = threadIdx.x; i <= ng; i += blockDim.x) s_rp[i] = rp[off + i];
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -87,25 +141,38 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   const int vstep = nwarps / Bw;
   long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
 
+  // the 32 trajectories of a warp are fixed, so what a pass needs is too
+  const bool w_drop = __any_sync(0xffffffffu, round == RD_DROP);
+  const bool w_comp = __any_sync(0xffffffffu, round == RD_COMPLETE);
+  const bool w_flip = __any_sync(0xffffffffu, round == RD_FLIP1);
+  const bool w_lane = __any_sync(0xffffffffu, round == RD_SWAP || round == RD_FLIP2);
+  const bool w_words = w_drop || w_comp || w_flip;
+  const bool w_act = __any_sync(0xffffffffu, round != RD_NONE);
+  const int vfirst = warp / Bw;
+
   // ---------------- pass A: decisions on the snapshot
-  for (int vl = warp / Bw; vl < ng; vl += vstep) {
+  NbList cur, nxt;
+  if ((w_words || w_lane) && vfirst < ng && w_words) nb_load(cur, s_rp, col, off, vfirst);
+  for (int vl = vfirst; (w_words || w_lane) && vl < ng; vl += vstep) {
+    if (w_words && vl + vstep < ng) nb_load(nxt, s_rp, col, off, vl + vstep);
     const int64_t v = off + vl;
-    const int32_t rs = rp[v], re = rp[v + 1];
+    const int32_t rs = s_rp[vl], re = s_rp[vl + 1];
     const int64_t e = v * B + b;
     const bool zv = sbit(sW, vl, Bw, b);
     bool dropv = false, addv = false, flipv = false;
-    if (__any_sync(0xffffffffu, round == RD_DROP)) {
-      const uint32_t o = warp_nb_or(sW, col, rs, re, off, Bw, wk, vl, true);
+    if (w_drop) {
+      const uint32_t o = nb_or(cur, sW, col, off, Bw, wk, vl, true);
       dropv = round == RD_DROP && zv && (o & bit);
     }
-    if (__any_sync(0xffffffffu, round == RD_COMPLETE)) {
-      const uint32_t o = warp_nb_or(sF, col, rs, re, off, Bw, wk, vl, true);
+    if (w_comp) {
+      const uint32_t o = nb_or(cur, sF, col, off, Bw, wk, vl, true);
       addv = round == RD_COMPLETE && sbit(sF, vl, Bw, b) && !(o & bit);
     }
-    if (__any_sync(0xffffffffu, round == RD_FLIP1)) {
-      const uint32_t o = warp_nb_or(sA, col, rs, re, off, Bw, wk, vl, true);
+    if (w_flip) {
+      const uint32_t o = nb_or(cur, sA, col, off, Bw, wk, vl, true);
       flipv = round == RD_FLIP1 && sbit(sA, vl, Bw, b) && !(o & bit);
     }
+    if (w_words) cur = nxt;
     const unsigned md = __ballot_sync(0xffffffffu, dropv);
     const unsigned mc = __ballot_sync(0xffffffffu, addv || flipv);
     if (lane == 0) {
@@ -160,7 +227,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   __syncthreads();
 
   // ---------------- pass B: commits
-  for (int vl = warp / Bw; vl < ng; vl += vstep) {
+  for (int vl = vfirst; (w_drop || w_lane) && vl < ng; vl += vstep) {
     const int64_t v = off + vl;
     const int64_t e = v * B + b;
     const unsigned md = sD[vl * Bw + wk];
@@ -216,27 +283,19 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
 
   // ---------------- pass C: counts of the (new) work set
   const bool act = round != RD_NONE;
-  for (int vl = warp / Bw; vl < ng; vl += vstep) {
+  if (w_act && mis && vfirst < ng) nb_load(cur, s_rp, col, off, vfirst);
+  for (int vl = vfirst; w_act && vl < ng; vl += vstep) {
+    if (mis && vl + vstep < ng) nb_load(nxt, s_rp, col, off, vl + vstep);
     const int64_t v = off + vl;
-    const int32_t rs = rp[v], re = rp[v + 1];
+    const int32_t rs = s_rp[vl], re = s_rp[vl + 1];
     const int64_t e = v * B + b;
     const bool zv = sbit(sW, vl, Bw, b);
     bool aux = false, fr = false;
     if (act) S.owner[e] = 0x7fffffff;
     if (mis) {
-      uint32_t once = 0u, twice = 0u;
-      for (int32_t j = rs + lane; j < re; j += 32) {
-        const uint32_t w = sW[(col[j] - off) * Bw + wk];
-        twice |= once & w;
-        once |= w;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, once, o);
-        const uint32_t t2 = __shfl_xor_sync(0xffffffffu, twice, o);
-        twice = twice | t2 | (once & o2);
-        once |= o2;
-      }
+      uint32_t once, twice;
+      nb_once_twice(cur, sW, col, off, Bw, wk, once, twice);
+      cur = nxt;
       if (act) {
         const bool one = (once & bit) != 0, two = (twice & bit) != 0;
         acc0 += zv;
@@ -293,7 +352,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
 
 size_t disc_graph_smem_bytes(int B, int max_ng) {
   const size_t nw = (size_t)max_ng * ((B + 31) / 32);
-  return 4 * nw * 4 + (size_t)((B + 1) & ~1) * 4 + 4 * (size_t)B * 8;
+  return 4 * nw * 4 + (size_t)((B + 1) & ~1) * 4 + 4 * (size_t)B * 8 + ((size_t)max_ng + 1) * 4;
 }
 
 cudaError_t launch_disc_graph(const SolverDev& S, size_t smem, cudaStream_t stream) {

@@ -332,43 +332,55 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     const int rs = has ? rp[v] : 0, re = has ? rp[v + 1] : 0;
     const int nch_w = __reduce_max_sync(0xffffffffu, (re - rs + LPR - 1) / LPR);
     int wsum = weighted ? 0 : re - rs;
-    // column indices of four chunks are loaded before any of them is used
+    // column indices come in groups of four chunks; the next group's loads
+    // are issued before the current group is consumed (software pipeline)
+    int nxu[4], nxw[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = rs + c * LPR + l;
+      const bool jin = j < re;
+      nxu[c] = jin ? __ldcs(col + j) - off : ng;
+      nxw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
+    }
     for (int ch0 = 0; ch0 < nch_w; ch0 += 4) {
-      int myu[4], myw[4];
+      int myo[4], myw[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int j = rs + (ch0 + c) * LPR + l;
-        const bool jin = j < re;
-        myu[c] = jin ? __ldcs(col + j) - off : ng;
-        myw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
+        if (MIS)
+          for (int w = 0; w < BW; ++w) orw[w] |= sZ[nxu[c] * BW + w];
+        myo[c] = nxu[c] * pitch;  // byte offset of the neighbour's row
+        myw[c] = nxw[c];
       }
-      if (MIS) {
+      if (ch0 + 4 < nch_w) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          for (int w = 0; w < BW; ++w) orw[w] |= sZ[myu[c] * BW + w];
+        for (int c = 0; c < 4; ++c) {
+          const int j = rs + (ch0 + 4 + c) * LPR + l;
+          const bool jin = j < re;
+          nxu[c] = jin ? __ldcs(col + j) - off : ng;
+          nxw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
+        }
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         if (ch0 + c >= nch_w) break;
 #pragma unroll
         for (int k = 0; k < LPR; ++k) {
-          const int u = __shfl_sync(0xffffffffu, myu[c], k, LPR);
-          const Pack<TX, VEC> p = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)u * pitch);
+          const int o = __shfl_sync(0xffffffffu, myo[c], k, LPR);
+          float f[VEC];
+          load_unpack<TX, VEC>(sXl + o, f);
           if (weighted) {
             const int w = __shfl_sync(0xffffffffu, myw[c], k, LPR);
             wsum += w;
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-              const float f = to_f(p.e[e]);
-              acc[e] = w >= 0 ? acc[e] + f : acc[e] - f;
-              pos[e] += (f > thr) ? w : 0;
+              acc[e] = w >= 0 ? acc[e] + f[e] : acc[e] - f[e];
+              pos[e] += (f[e] > thr) ? w : 0;
             }
           } else {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-              const float f = to_f(p.e[e]);
-              acc[e] = acc[e] + f;
-              if (!MIS) pos[e] += (f > thr);
+              acc[e] = acc[e] + f[e];
+              if (!MIS) pos[e] += (f[e] > thr);
             }
           }
         }
