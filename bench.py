@@ -27,6 +27,7 @@ import sys
 import tempfile
 import threading
 import time
+import types
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -225,15 +226,16 @@ def algorithmic_bytes_per_step(G, B, sx, sv):
     return G.nnz * 4 + (n + 1) * 4 + 2 * n * B * sx + 2 * n * B * sv + n * bw * 4
 
 
-def step_kernel_traffic(workload, x_dtype):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    or None if the kernel source changed since the capture."""
+def step_kernel_traffic(workload, x_dtype, variant):
+    """Per-launch DRAM bytes of the step kernel variant (smem, smem_wide,
+    global) from the committed ncu summary, or None if there is none or the
+    kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}_{x_dtype}.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    t = re.search(r"dram_bytes_per_launch\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", txt)
     if not m or not t:
         return None
     h = hashlib.sha256()
@@ -277,10 +279,11 @@ def gpu_arm(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    def measure(x_dtype, v_dtype, steps, warmup, sample_clocks):
+    def measure(x_dtype, v_dtype, steps, warmup, sample_clocks, autotune=False):
         g = mq.Graph(G)
         s = mq.Solver(g, mq.params(x_dtype=x_dtype, v_dtype=v_dtype, **pkw))
         s.run(warmup)
+        tuned = s.autotune(10) if autotune else None
         torch.cuda.synchronize()
         barrier()
         sampler = ClockSampler(local) if sample_clocks else None
@@ -300,49 +303,88 @@ def gpu_arm(args):
         clocks = sampler.summary() if sampler else None
         vals, _ = s.best(want_bits=False)
         info = s.info()
+        if tuned:
+            info["autotune_ms_per_tick"] = tuned["ms_per_tick"]
         s.close()
         g.close()
         return ms, phase_ms, clocks, vals, info
 
     nnz_b = G.nnz * B
-    ms, phase_ms, clocks, best_vals, plan = measure(xd, vd, args.steps, args.warmup, True)
+    ms, phase_ms, clocks, best_vals, plan = measure(xd, vd, args.steps, args.warmup, True, not args.no_autotune)
     step_avg_ms = phase_ms["step"] / args.steps
     ms, value = aggregate_ranks(ms, float(nnz_b) * args.steps, dist, "cuda")
 
     # the plain FP32-state form of the same workload, for comparison
     f32 = None
+    single = None
     if xd != 0 and not args.no_compare:
-        k32 = max(1, args.steps // 2)
-        ms32, ph32, _, _, _ = measure(0, 0, k32, args.warmup, False)
-        f32 = {"value": nnz_b * k32 / (ms32 / 1e3), "ms_per_step": ms32 / k32, "step_kernel_ms": ph32["step"] / k32}
+        k32 = args.steps
+        ms32, ph32, _, vals32, _ = measure(0, 0, k32, args.warmup, False)
+        f32 = {"value": nnz_b * k32 / (ms32 / 1e3), "ms_per_step": ms32 / k32, "step_kernel_ms": ph32["step"] / k32,
+               "best_mean": float(np.mean(vals32)), "best_max": int(np.max(vals32)), "ticks": args.warmup + k32}
+        if G.num_graphs > 1:
+            # the plain form: member graph 0 alone, FP32 state, the same B
+            # trajectories (keyed by graph and slot, so identical to the
+            # batch's first B) and the same number of ticks
+            G0 = G.subgraph(0)
+            g0 = mq.Graph(G0)
+            s0 = mq.Solver(g0, mq.params(x_dtype=0, v_dtype=0, **pkw))
+            s0.run(args.warmup)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s0.run(args.steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms0 = e0.elapsed_time(e1)
+            vals0, _ = s0.best(want_bits=False)
+            s0.close()
+            g0.close()
+            single = {"value": G0.nnz * B * args.steps / (ms0 / 1e3), "unit": UNIT, "ms_per_step": ms0 / args.steps,
+                      "graph": f"member graph 0 alone (n={G0.n}, nnz={G0.nnz}), B={B}, f32 state",
+                      "best_mean": float(np.mean(vals0)), "batched_bf16_best_mean_same_graph": float(np.mean(best_vals[:B])),
+                      "batched_f32_best_mean_same_graph": float(np.mean(vals32[:B])), "ticks": args.warmup + args.steps}
 
     # end to end through the public API with host buffers: graph upload from
-    # host arrays, solver creation, every tick followed by a device->host
-    # read of the per-trajectory best values
+    # pinned host arrays (validated on the host), solver creation, every tick
+    # followed by a device->host read of the per-trajectory best values
+    def pinned(a):
+        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    Gp = types.SimpleNamespace(n=G.n, row_ptr=pinned(G.row_ptr.astype(np.int64)),
+                               col_idx=pinned(G.col_idx.astype(np.int32)),
+                               weights=None if G.weights is None else pinned(G.weights.astype(np.int8)),
+                               node_offsets=G.node_offsets)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    g = mq.Graph(G)
+    g = mq.Graph(Gp)
+    t1 = time.perf_counter()
     s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **pkw))
+    t2 = time.perf_counter()
     e2e_steps = args.steps
     for _ in range(e2e_steps):
         s.run(1)
         vals, _ = s.best(want_bits=False)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    t_e2e = t3 - t0
     s.close()
     g.close()
     ms_e2e, e2e_value = aggregate_ranks(t_e2e * 1e3, float(nnz_b) * e2e_steps, dist, "cuda")
     csr_bytes = G.nnz * 4 + (G.n + 1) * 8 + (G.nnz if G.weights is not None else 0) + 8 * (G.num_graphs + 1)
     e2e = {"value": e2e_value, "unit": UNIT,
-           "h2d_bytes_per_step": int(csr_bytes / e2e_steps), "d2h_bytes_per_step": int(8 * G.num_graphs * B)}
+           "h2d_bytes_per_step": int(csr_bytes / e2e_steps), "d2h_bytes_per_step": int(8 * G.num_graphs * B),
+           "graph_upload_ms": (t1 - t0) * 1e3, "solver_create_ms": (t2 - t1) * 1e3,
+           "ticks_ms": (t3 - t2) * 1e3, "steps": e2e_steps}
 
     alg = algorithmic_bytes_per_step(G, B, sx, sv)
     hbm_achieved = alg / (step_avg_ms / 1e3) / 1e9
     hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
            "frac": hbm_achieved / hbm_peak, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
-    traffic = step_kernel_traffic(args.workload, args.x_dtype)
-    if plan["step_kernel"] == "smem":
+    traffic = step_kernel_traffic(args.workload, args.x_dtype, plan["step_kernel"])
+    if plan["step_kernel"].startswith("smem"):
         # every neighbour row of x is read from shared memory once per step:
         # nnz * B * sx bytes; peak = one 128-byte wavefront per clock per SM
         sm_clock = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
@@ -356,7 +398,7 @@ def gpu_arm(args):
                 "algorithmic_bytes_per_launch": gathered, "hbm": hbm}
     else:
         roof = dict(hbm, traffic=traffic)
-    roof.update(kernel="mqo::k_step_s" if plan["step_kernel"] == "smem" else "mqo::k_step_g",
+    roof.update(kernel="mqo::k_step_s" if plan["step_kernel"].startswith("smem") else "mqo::k_step_g",
                 step_kernel_ms=step_avg_ms, plan=plan)
 
     cpu = None
@@ -377,6 +419,8 @@ def gpu_arm(args):
         }
         if f32:
             line["fp32_state"] = f32
+        if single:
+            line["single_instance_fp32"] = single
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))
@@ -396,6 +440,7 @@ def main():
     ap.add_argument("--v-dtype", default=None, choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -249,17 +249,36 @@ MQO_API mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits);
 MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
 
 /*
- * Execution plan chosen at creation (host, any pointer may be NULL):
- * *step_kernel bit 0 = the fused step stages each member graph's block of x
- * in shared memory (every member graph fits; else the global-memory
- * kernel), bit 1 = the discrete passes run fused, one CTA per member graph
- * (else three node-parallel launches); *smem_bytes = the step kernel's
+ * Execution plan (chosen at creation or by mqo_autotune; host, any pointer
+ * may be NULL): *step_kernel bit 0 = the fused step stages each member
+ * graph's block of x in shared memory (every member graph fits; else the
+ * global-memory kernel), bit 1 = the discrete passes run fused, one CTA per
+ * member graph (else three node-parallel launches), bit 2 = the
+ * shared-memory step kernel uses 16-byte lanes (twice the trajectories per
+ * lane, twice the rows per warp), bits 4.. = trajectories per lane of the
+ * global-memory step kernel (0 with bit 0); *smem_bytes = the step kernel's
  * dynamic shared memory per CTA; *items = CTAs
  * per step (node ranges of at most 256 nodes); *replicas = counter
  * replicas per trajectory.
  */
 MQO_API mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_bytes, int32_t* items,
                                    int32_t* replicas);
+
+/*
+ * Autotuner of the launch plan: every plan the solver can run (shared-memory
+ * or global-memory step kernel, for the latter each choice of trajectories
+ * per lane, i.e. lanes per row, and fused or node-parallel discrete passes)
+ * runs `ticks` machine ticks from the current state; the state is restored
+ * after every trial, so tuning changes no result (all plans compute the same
+ * ticks bit for bit).  The fastest plan is kept for later ticks.  Writes the
+ * plan to *plan (bit 0 shared-memory step, bit 1 fused discrete passes,
+ * bit 2 16-byte lanes of the shared-memory step, bits 4.. trajectories per
+ * lane of the global-memory step kernel, 0 when bit 0 is set) and its time
+ * per tick in milliseconds to *ms_per_tick
+ * (either may be NULL).  Allocates a snapshot of the solver's state for the
+ * duration of the call and synchronises.
+ */
+MQO_API mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan, double* ms_per_tick);
 
 /* Copy the current relaxed iterate X (n*B values of x_dtype, node-major)
  * to / from device memory.  During a discrete phase a trajectory's x is

@@ -86,6 +86,7 @@ _SIGS = {
     "mqo_best": [_P, _P, _P],
     "mqo_traj_state": [_P, _P],
     "mqo_solver_info": [_P, _P, _P, _P, _P],
+    "mqo_autotune": [_P, C.c_int32, _P, _P],
     "mqo_get_x": [_P, _P],
     "mqo_set_x": [_P, _P],
     "mqo_get_v": [_P, _P],
@@ -271,9 +272,18 @@ class Solver:
         """Execution plan: step kernel (1 shared-memory staged, 0 global), smem bytes, items, counter replicas."""
         k, sm, it, r = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
         _check(lib().mqo_solver_info(self.handle, C.byref(k), C.byref(sm), C.byref(it), C.byref(r)))
-        return {"step_kernel": "smem" if k.value & 1 else "global",
-                "discrete_kernel": "graph" if k.value & 2 else "pairs", "smem_bytes": sm.value, "items": it.value,
-                "replicas": r.value}
+        return {"step_kernel": ("smem_wide" if k.value & 4 else "smem") if k.value & 1 else "global",
+                "discrete_kernel": "graph" if k.value & 2 else "pairs", "lanes_vec": k.value >> 4,
+                "smem_bytes": sm.value, "items": it.value, "replicas": r.value}
+
+    def autotune(self, ticks=10):
+        """Time every launch plan over `ticks` ticks (state restored after each) and keep the fastest."""
+        plan, ms = C.c_int32(), C.c_double()
+        _check(lib().mqo_autotune(self.handle, int(ticks), C.byref(plan), C.byref(ms)))
+        p = plan.value
+        return {"step_kernel": ("smem_wide" if p & 4 else "smem") if p & 1 else "global",
+                "discrete_kernel": "graph" if p & 2 else "pairs",
+                "lanes_vec": p >> 4, "ms_per_tick": ms.value}
 
     def traj_state(self):
         arr = (TrajInfo * self.T)()

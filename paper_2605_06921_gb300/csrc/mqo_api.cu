@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mqo.h"
@@ -33,7 +34,7 @@ mqo_status fail(mqo_status st, const char* fmt, ...) {
   return st;
 }
 
-constexpr int kChunkNodes = 256;  // nodes per item
+constexpr int kChunkNodes = kItemMaxNodes;  // nodes per item
 constexpr int kSplit = 512;       // row length above which the f_B kernels chunk a row
 constexpr size_t kStepSmemLimit = 110 * 1024;  // shared-memory step kernel if the graph block fits
 constexpr size_t kDiscSmemLimit = 96 * 1024;   // fused discrete kernel if the graph's bit words fit
@@ -55,6 +56,7 @@ struct mqo_graph_s {
   int32_t* d_off = nullptr;
   int32_t* d_dmax = nullptr;
   Item* d_items = nullptr;
+  int32_t* d_order = nullptr;
   int32_t num_items = 0;
   std::vector<int32_t> h_rp;
   std::vector<int32_t> h_off;
@@ -78,6 +80,7 @@ struct mqo_graph_s {
     g.node_off = d_off;
     g.dmax = d_dmax;
     g.items = d_items;
+    g.order = d_order;
     g.num_items = num_items;
     return g;
   }
@@ -95,6 +98,8 @@ struct mqo_solver_s {
   int grid = 1;
   size_t step_smem = 0;  // > 0: shared-memory step kernel with this much dynamic smem
   size_t disc_smem = 0;  // > 0: fused per-graph discrete kernel with this much dynamic smem
+  size_t step_smem_max = 0;  // smem the shared-memory step kernel needs (0: not possible)
+  size_t disc_smem_max = 0;  // smem the fused discrete kernel needs (0: not possible)
   int64_t host_tick = 0;
   Counters* d_cnt_plain = nullptr;
   Counters* d_eval = nullptr;
@@ -134,24 +139,66 @@ mqo_status validate(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* co
     for (int32_t g = 0; g < G; ++g)
       for (int64_t v = offs[g]; v < offs[g + 1]; ++v) graph_of[(size_t)v] = g;
   }
-  for (int64_t v = 0; v < n; ++v) {
-    for (int64_t j = rp[v]; j < rp[v + 1]; ++j) {
-      const int32_t u = col[j];
-      if (u < 0 || u >= n) return fail(MQO_EGRAPH, "col_idx[%lld]=%d out of range", (long long)j, u);
-      if (u == v) return fail(MQO_EGRAPH, "self loop at node %lld", (long long)v);
-      if (j > rp[v] && col[j - 1] >= u)
-        return fail(MQO_EGRAPH, "row %lld not strictly ascending at entry %lld", (long long)v, (long long)j);
-      if (w && w[j] != 1 && w[j] != -1) return fail(MQO_EGRAPH, "weight %d at entry %lld not in {-1,+1}", w[j], (long long)j);
-      if (offs && graph_of[(size_t)u] != graph_of[(size_t)v])
-        return fail(MQO_EGRAPH, "edge (%lld,%d) joins two member graphs", (long long)v, u);
-      // symmetric: v in row u with the same weight
-      const int32_t* b = col + rp[u];
-      const int32_t* e = col + rp[u + 1];
-      const int32_t* f = std::lower_bound(b, e, (int32_t)v);
-      if (f == e || *f != v) return fail(MQO_EGRAPH, "edge (%lld,%d) has no reverse entry", (long long)v, u);
-      if (w && w[rp[u] + (f - b)] != w[j]) return fail(MQO_EGRAPH, "weight of (%lld,%d) is not symmetric", (long long)v, u);
+  // rows are checked in parallel ranges; the reported error is the one of
+  // the smallest row, as a sequential scan would find it
+  struct Bad {
+    int64_t row = -1;
+    char msg[200] = {0};
+  };
+  auto check_rows = [&](int64_t v0, int64_t v1, Bad* bad) {
+    for (int64_t v = v0; v < v1; ++v) {
+      for (int64_t j = rp[v]; j < rp[v + 1]; ++j) {
+        const int32_t u = col[j];
+        const char* why = nullptr;
+        char buf[200];
+        if (u < 0 || u >= n) {
+          snprintf(buf, sizeof(buf), "col_idx[%lld]=%d out of range", (long long)j, u);
+          why = buf;
+        } else if (u == v) {
+          snprintf(buf, sizeof(buf), "self loop at node %lld", (long long)v);
+          why = buf;
+        } else if (j > rp[v] && col[j - 1] >= u) {
+          snprintf(buf, sizeof(buf), "row %lld not strictly ascending at entry %lld", (long long)v, (long long)j);
+          why = buf;
+        } else if (w && w[j] != 1 && w[j] != -1) {
+          snprintf(buf, sizeof(buf), "weight %d at entry %lld not in {-1,+1}", w[j], (long long)j);
+          why = buf;
+        } else if (offs && graph_of[(size_t)u] != graph_of[(size_t)v]) {
+          snprintf(buf, sizeof(buf), "edge (%lld,%d) joins two member graphs", (long long)v, u);
+          why = buf;
+        } else {
+          // symmetric: v in row u with the same weight
+          const int32_t* b = col + rp[u];
+          const int32_t* e = col + rp[u + 1];
+          const int32_t* f = std::lower_bound(b, e, (int32_t)v);
+          if (f == e || *f != v) {
+            snprintf(buf, sizeof(buf), "edge (%lld,%d) has no reverse entry", (long long)v, u);
+            why = buf;
+          } else if (w && w[rp[u] + (f - b)] != w[j]) {
+            snprintf(buf, sizeof(buf), "weight of (%lld,%d) is not symmetric", (long long)v, u);
+            why = buf;
+          }
+        }
+        if (why) {
+          bad->row = v;
+          snprintf(bad->msg, sizeof(bad->msg), "%s", why);
+          return;
+        }
+      }
     }
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int P = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, nnz / 65536 + 1}));
+  std::vector<Bad> bad((size_t)P);
+  std::vector<std::thread> pool;
+  for (int p = 0; p < P; ++p) {
+    const int64_t v0 = n * p / P, v1 = n * (p + 1) / P;
+    if (p == P - 1) check_rows(v0, v1, &bad[(size_t)p]);
+    else pool.emplace_back(check_rows, v0, v1, &bad[(size_t)p]);
   }
+  for (auto& th : pool) th.join();
+  for (const Bad& b : bad)
+    if (b.row >= 0) return fail(MQO_EGRAPH, "%s", b.msg);
   return MQO_OK;
 }
 
@@ -220,6 +267,15 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
       items.push_back(it);
     }
   }
+  // rows of every item by decreasing degree (ties by node id): rows that
+  // walk their neighbour lists in lockstep then have nearly equal lengths
+  std::vector<int32_t> order((size_t)n);
+  for (const Item& it : items) {
+    int32_t* o = order.data() + it.v0;
+    for (int32_t v = it.v0; v < it.v1; ++v) o[v - it.v0] = v;
+    std::stable_sort(o, o + (it.v1 - it.v0),
+                     [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+  }
   g->num_items = (int32_t)items.size();
   g->h_items = items;
   g->h_off = off32;
@@ -233,6 +289,7 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   if ((st = dalloc(&g->d_off, (size_t)G + 1, nullptr)) != MQO_OK) return cleanup(st);
   if ((st = dalloc(&g->d_dmax, (size_t)G, nullptr)) != MQO_OK) return cleanup(st);
   if ((st = dalloc(&g->d_items, items.size(), nullptr)) != MQO_OK) return cleanup(st);
+  if ((st = dalloc(&g->d_order, (size_t)n, nullptr)) != MQO_OK) return cleanup(st);
   cudaError_t e = cudaSuccess;
   e = cudaMemcpy(g->d_rp, g->h_rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nnz) e = cudaMemcpy(g->d_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
@@ -240,6 +297,7 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   if (e == cudaSuccess) e = cudaMemcpy(g->d_off, off32.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_dmax, dmax.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cleanup(fail(MQO_ECUDA, "graph upload: %s", cudaGetErrorString(e)));
   *out = g;
   return MQO_OK;
@@ -417,6 +475,7 @@ mqo_status mqo_graph_destroy(mqo_graph g) {
   cudaFree(g->d_off);
   cudaFree(g->d_dmax);
   cudaFree(g->d_items);
+  cudaFree(g->d_order);
   cudaFree(g->d_hp);
   cudaFree(g->d_scratch);
   delete g;
@@ -514,18 +573,23 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     // when the member graphs fit in shared memory
     const char* force = getenv("MQO_STEP_KERNEL");
     const bool generic = force && strcmp(force, "generic") == 0;
-    s->step_smem = (!generic && B >= 32 && need <= kStepSmemLimit) ? need : 0;
+    s->step_smem_max = (B >= 32 && need <= kStepSmemLimit) ? need : 0;
+    s->step_smem = generic ? 0 : s->step_smem_max;
+    // MQO_STEP_KERNEL=wide: the shared-memory kernel with 16-byte lanes
+    s->S.step_wide = force && strcmp(force, "wide") == 0 && step_wide_possible(B, p->x_dtype) ? 1 : 0;
     // MQO_DISC_KERNEL=pairs selects the three node-parallel discrete passes
     // even when every member graph's bit words fit in shared memory
     const char* dforce = getenv("MQO_DISC_KERNEL");
     const bool pairs = dforce && strcmp(dforce, "pairs") == 0;
     const size_t dneed = disc_graph_smem_bytes(B, max_ng);
-    s->disc_smem = (!pairs && B >= 32 && dneed <= kDiscSmemLimit) ? dneed : 0;
+    s->disc_smem_max = (B >= 32 && dneed <= kDiscSmemLimit) ? dneed : 0;
+    s->disc_smem = pairs ? 0 : s->disc_smem_max;
   }
   const size_t TR = (size_t)T * S.R;
   if ((st = dalloc(&S.st, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.act, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.rnd, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  if ((st = dalloc(&S.bestv, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.cnt, TR, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&s->d_cnt_plain, TR, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&s->d_eval, TR, &s->allocs)) != MQO_OK) return bail(st);
@@ -777,13 +841,9 @@ mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits) {
   {
     Scope sc(s);
     if (z_bits) CKS(cudaMemcpyAsync(z_bits, S.Zbest, s->words * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s->work));
+    if (values) CKS(cudaMemcpyAsync(values, S.bestv, T * sizeof(int64_t), cudaMemcpyDeviceToHost, s->work));
   }
-  if (values) {
-    std::vector<TrajState> h(T);
-    CKS(cudaStreamSynchronize(s->work));
-    CKS(cudaMemcpy(h.data(), S.st, T * sizeof(TrajState), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < T; ++i) values[i] = h[i].best;
-  }
+  CKS(cudaStreamSynchronize(s->work));
   CKS(cudaStreamSynchronize(s->user));
   return MQO_OK;
 }
@@ -791,7 +851,11 @@ mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits) {
 mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_bytes, int32_t* items,
                            int32_t* replicas) {
   if (!s) return fail(MQO_EINVAL, "null solver");
-  if (step_kernel) *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0);
+  const int B = s->S.B;
+  const int vec = s->step_smem > 0 ? 0 : (s->S.step_vec > 0 ? s->S.step_vec : (B >= 32 ? B / 32 : 1));
+  if (step_kernel)
+    *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0) |
+                   (s->step_smem > 0 && s->S.step_wide ? 4 : 0) | (vec << 4);
   if (smem_bytes) *smem_bytes = (int64_t)s->step_smem;
   if (items) *items = s->S.g.num_items;
   if (replicas) *replicas = s->S.R;
@@ -933,6 +997,119 @@ mqo_status mqo_pga_adam_step(float* x, float* m, float* u, const float* grad, in
                              float b2, float eps, int64_t t, float lo, float hi, void* cuda_stream) {
   if (count < 0 || (count > 0 && (!x || !m || !u || !grad)) || t < 1) return fail(MQO_EINVAL, "bad argument");
   CKG(launch_adam(x, m, u, grad, count, lr, b1, b2, eps, t, lo, hi, (cudaStream_t)cuda_stream));
+  return MQO_OK;
+}
+
+mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* best_ms_per_tick) {
+  CHECK_SOLVER(s);
+  if (ticks < 1) return fail(MQO_EINVAL, "ticks must be >= 1");
+  SolverDev& S = s->S;
+  const int B = S.B;
+  const size_t T = (size_t)S.g.num_graphs * B;
+  // every mutable device buffer of the solver, saved and restored around
+  // each trial so that tuning leaves the trajectories where they were
+  struct Buf {
+    void* p;
+    size_t n;
+  };
+  const std::vector<Buf> bufs = {
+      {S.X0, s->x_bytes}, {S.X1, s->x_bytes}, {S.V, s->v_bytes},
+      {S.ZX0, s->words * 4}, {S.ZX1, s->words * 4}, {S.Zbest, s->words * 4}, {S.Zwork, s->words * 4},
+      {S.Zaux, s->words * 4}, {S.Zfree, s->words * 4}, {S.Zdrop, s->words * 4},
+      {S.owner, s->pairs * 4}, {S.pa, s->pairs * 4}, {S.pb, s->pairs * 4}, {S.gain, s->pairs * 4},
+      {S.st, T * sizeof(TrajState)}, {S.act, T * 4}, {S.rnd, T * 4}, {S.bestv, T * 8},
+      {S.cnt, T * S.R * sizeof(Counters)}, {S.tick, 8}, {S.gflag, (size_t)3 * S.g.num_graphs * 4}, {S.any, 16}};
+  size_t total = 0;
+  for (const Buf& b : bufs) total += (b.n + 255) & ~(size_t)255;
+  char* snap = nullptr;
+  CKS(cudaMalloc(&snap, total));
+  struct Plan {
+    size_t step_smem;
+    int vec;
+    int wide;
+    size_t disc_smem;
+  };
+  std::vector<Plan> plans;
+  std::vector<size_t> steps = {0};
+  if (s->step_smem_max > 0) steps.push_back(s->step_smem_max);
+  std::vector<size_t> discs = {0};
+  if (s->disc_smem_max > 0) discs.push_back(s->disc_smem_max);
+  const bool wide_ok = step_wide_possible(B, S.p.x_dtype);
+  for (size_t st : steps)
+    for (size_t dc : discs) {
+      if (st > 0) {
+        plans.push_back({st, 0, 0, dc});
+        if (wide_ok) plans.push_back({st, 0, 1, dc});
+      } else {
+        for (int v : {1, 2, 4})
+          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc});
+      }
+    }
+  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  double best = 1e300;
+  Plan chosen = keep;
+  {
+    Scope sc(s);
+    size_t off = 0;
+    for (const Buf& b : bufs) {
+      if (err == cudaSuccess) err = cudaMemcpyAsync(snap + off, b.p, b.n, cudaMemcpyDeviceToDevice, s->work);
+      off += (b.n + 255) & ~(size_t)255;
+    }
+    for (const Plan& pl : plans) {
+      if (err != cudaSuccess) break;
+      off = 0;
+      for (const Buf& b : bufs) {
+        if (err == cudaSuccess) err = cudaMemcpyAsync(b.p, snap + off, b.n, cudaMemcpyDeviceToDevice, s->work);
+        off += (b.n + 255) & ~(size_t)255;
+      }
+      s->step_smem = pl.step_smem;
+      S.step_vec = pl.vec;
+      S.step_wide = pl.wide;
+      s->disc_smem = pl.disc_smem;
+      if (err == cudaSuccess) err = enqueue_tick(s);  // untimed first tick
+      if (err == cudaSuccess) err = cudaEventRecord(e0, s->work);
+      for (int32_t k = 0; k < ticks && err == cudaSuccess; ++k) err = enqueue_tick(s);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, s->work);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        chosen = pl;
+      }
+    }
+    off = 0;
+    for (const Buf& b : bufs) {
+      if (err == cudaSuccess) err = cudaMemcpyAsync(b.p, snap + off, b.n, cudaMemcpyDeviceToDevice, s->work);
+      off += (b.n + 255) & ~(size_t)255;
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s->work);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(snap);
+  if (err != cudaSuccess) {
+    s->step_smem = keep.step_smem;
+    S.step_vec = keep.vec;
+    S.step_wide = keep.wide;
+    s->disc_smem = keep.disc_smem;
+    return poison(s, err, "mqo_autotune");
+  }
+  s->step_smem = chosen.step_smem;
+  S.step_vec = chosen.vec;
+  S.step_wide = chosen.wide;
+  s->disc_smem = chosen.disc_smem;
+  // the captured tick graphs hold the old launch configuration
+  if (s->gx1) cudaGraphExecDestroy(s->gx1);
+  if (s->gx16) cudaGraphExecDestroy(s->gx16);
+  s->gx1 = s->gx16 = nullptr;
+  if (plan_out)
+    *plan_out = (chosen.step_smem > 0 ? 1 : 0) | (chosen.disc_smem > 0 ? 2 : 0) | (chosen.wide ? 4 : 0) |
+                (chosen.vec << 4);
+  if (best_ms_per_tick) *best_ms_per_tick = best / ticks;
   return MQO_OK;
 }
 

@@ -64,6 +64,8 @@ struct Counters {
 };
 
 // A contiguous node range inside one member graph.
+constexpr int kItemMaxNodes = 256;  // nodes of one work item (a node range of one member graph)
+
 struct Item {
   int32_t g, v0, v1, pad;
 };
@@ -77,6 +79,7 @@ struct GraphDev {
   const int32_t* node_off;  // num_graphs+1
   const int32_t* dmax;      // num_graphs
   const Item* items;
+  const int32_t* order;     // n: the rows of each item [v0,v1) by decreasing degree
   int32_t num_items;
 };
 
@@ -85,6 +88,8 @@ struct SolverDev {
   Params p;
   int32_t B, Bw;
   int32_t R;        // counter replicas per trajectory (item i adds into replica i % R)
+  int32_t step_vec; // trajectories per lane of the global-memory step kernel (0: B/32 or 1)
+  int32_t step_wide; // shared-memory step kernel with 16-byte lanes
   void* X0;         // relaxed x: tick t reads X[t&1] and writes X[(t+1)&1]
   void* X1;
   void* V;          // momentum
@@ -106,6 +111,7 @@ struct SolverDev {
   int64_t* tick;    // current tick number
   int32_t* gflag;   // [3*G] tick stamps: any apply / any discrete / any step
   int32_t* any;     // [4] per-tick "any trajectory" stamps (apply, disc, step)
+  int64_t* bestv;   // [G*B] best value of each trajectory (compact copy for readout)
 };
 
 // sum of the R replicas of a trajectory's counters
@@ -262,6 +268,29 @@ __device__ __forceinline__ void load_unpack<__nv_bfloat16, 4>(const unsigned cha
   f[3] = __uint_as_float(r.y & 0xffff0000u);
 }
 template <>
+__device__ __forceinline__ void load_unpack<__nv_bfloat16, 8>(const unsigned char* p, float* f) {
+  const uint4 r = *reinterpret_cast<const uint4*>(p);
+  f[0] = __uint_as_float(r.x << 16);
+  f[1] = __uint_as_float(r.x & 0xffff0000u);
+  f[2] = __uint_as_float(r.y << 16);
+  f[3] = __uint_as_float(r.y & 0xffff0000u);
+  f[4] = __uint_as_float(r.z << 16);
+  f[5] = __uint_as_float(r.z & 0xffff0000u);
+  f[6] = __uint_as_float(r.w << 16);
+  f[7] = __uint_as_float(r.w & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void load_unpack<__half, 8>(const unsigned char* p, float* f) {
+  const uint4 r = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+    f[2 * k] = a.x;
+    f[2 * k + 1] = a.y;
+  }
+}
+template <>
 __device__ __forceinline__ void load_unpack<__half, 4>(const unsigned char* p, float* f) {
   const uint2 r = *reinterpret_cast<const uint2*>(p);
   const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
@@ -296,6 +325,18 @@ __device__ __forceinline__ void load_unpack<float, 4>(const unsigned char* p, fl
   f[1] = r.y;
   f[2] = r.z;
   f[3] = r.w;
+}
+
+// (a, b) += (x, y) with one packed FP32 add (sm_100 family): each element
+// is an IEEE round-to-nearest addition, bit-identical to a + x and b + y
+__device__ __forceinline__ void add_f32x2(float& a, float& b, float x, float y) {
+  asm("{\n\t.reg .b64 p, q;\n\t"
+      "mov.b64 p, {%0, %1};\n\t"
+      "mov.b64 q, {%2, %3};\n\t"
+      "add.rn.f32x2 p, p, q;\n\t"
+      "mov.b64 {%0, %1}, p;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "f"(x), "f"(y));
 }
 
 __device__ __forceinline__ float clamp_box(float v, float lo, float hi) {

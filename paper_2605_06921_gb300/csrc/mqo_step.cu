@@ -95,17 +95,28 @@ __device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float 
 // atomic per trajectory and counter into replica (item % R)
 template <int VEC>
 __device__ __forceinline__ void flush_step_counters(const StepArgs& a, unsigned long long* s_cnt, int g, int it,
-                                                    int b0, const int* c0, const int* c1, const int* c2,
-                                                    const bool* stepping) {
-  const int B = a.B;
+                                                    int b0, int lpr, int* c0, int* c1, int* c2,
+                                                    uint32_t stepm) {
+  // the 32/lpr row groups of a warp hold the same trajectories: sum them
+  // by shuffles first, so one lane per trajectory issues the atomics
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) {
-    if (!stepping[e]) continue;
-    if (c0[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 0], (unsigned long long)(long long)c0[e]);
-    if (c1[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 1], (unsigned long long)(long long)c1[e]);
-    if (c2[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 2], (unsigned long long)(long long)c2[e]);
+  for (int e = 0; e < VEC; ++e)
+    for (int o = lpr; o < 32; o <<= 1) {
+      c0[e] += __shfl_xor_sync(0xffffffffu, c0[e], o);
+      c1[e] += __shfl_xor_sync(0xffffffffu, c1[e], o);
+      c2[e] += __shfl_xor_sync(0xffffffffu, c2[e], o);
+    }
+  if ((threadIdx.x & 31) < lpr) {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      if (!((stepm >> e) & 1u)) continue;
+      if (c0[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 0], (unsigned long long)(long long)c0[e]);
+      if (c1[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 1], (unsigned long long)(long long)c1[e]);
+      if (c2[e]) atomicAdd(&s_cnt[3 * (b0 + e) + 2], (unsigned long long)(long long)c2[e]);
+    }
   }
   __syncthreads();
+  const int B = a.B;
   const int rep = it % a.R;
   for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) {
     const unsigned long long val = s_cnt[i];
@@ -153,9 +164,10 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
   const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;  // lanes sharing one output bit word
   const unsigned rmask = lpr == 32 ? 0xffffffffu : (((1u << lpr) - 1u) << (sub * lpr));
 
-  bool stepping[VEC];
+  uint32_t stepm = 0u;  // bit e: trajectory b0 + e steps
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) stepping[e] = a.act ? (a.act[(int64_t)g * B + b0 + e] & ACT_STEP) != 0 : true;
+  for (int e = 0; e < VEC; ++e)
+    stepm |= (uint32_t)(a.act ? (a.act[(int64_t)g * B + b0 + e] & ACT_STEP) != 0 : true) << e;
   int c0[VEC], c1[VEC], c2[VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
@@ -216,7 +228,8 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       bool zn;
-      step_element<TX, TV>(a, mis, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, stepping[e], xo.e[e], vo.e[e],
+      step_element<TX, TV>(a, mis, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, (stepm >> e) & 1u, xo.e[e],
+                           vo.e[e],
                            zn, c0[e], c1[e], c2[e]);
       zbits |= (unsigned)zn << e;
     }
@@ -226,7 +239,7 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
     for (int off = 1; off < K; off <<= 1) word |= __shfl_xor_sync(rmask, word, off);
     if ((l % K) == 0) Zn[(int64_t)v * a.Bw + (b0 >> 5)] = word;
   }
-  flush_step_counters<VEC>(a, s_cnt, g, it, b0, c0, c1, c2, stepping);
+  flush_step_counters<VEC>(a, s_cnt, g, it, b0, lpr, c0, c1, c2, stepm);
 }
 
 // ---------------------------------------------------------------- shared memory
@@ -234,7 +247,9 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
 // group of LPR = B/VEC lanes one node, and the RPW = 32/LPR row groups of a
 // warp walk their rows' neighbour lists in lockstep, LPR neighbours (one
 // chunk) at a time, so one shuffle and one shared-memory load instruction
-// serve RPW rows.  Rows shorter than the warp's longest are padded with a
+// serve RPW rows.  An item's rows are taken in decreasing-degree order, so
+// the rows of a warp have nearly equal lengths; rows shorter than the
+// warp's longest are padded with a
 // dummy neighbour, local index ng, whose shared-memory row of x and bit
 // words are zero: adding +0.0 leaves a float32 sum that is not -0.0
 // unchanged, and sums of values that are never -0.0 are never -0.0, so the
@@ -252,8 +267,8 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   const int g = item.g;
   const int64_t t = *a.tick;
   if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
-  const int B = a.B;
-  const int BW = a.Bw;
+  constexpr int B = VEC * LPR;  // a row group of LPR lanes holds the whole batch
+  constexpr int BW = (B + 31) / 32;
   const int32_t off = a.g.node_off[g];
   const int32_t ng = a.g.node_off[g + 1] - off;
   const int rowb = B * (int)sizeof(TX);  // bytes of one node's x
@@ -262,6 +277,9 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   uint32_t* sZ = reinterpret_cast<uint32_t*>(smem + xbytes);
   const size_t zbytes = MIS ? (((size_t)(ng + 1) * BW * 4 + 15) & ~(size_t)15) : 0;
   unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem + xbytes + zbytes);
+  // the item's rows in processing order: {node, row start, row end}
+  int4* s_rows = reinterpret_cast<int4*>(smem + xbytes + zbytes + ((3 * (size_t)B * 8 + 15) & ~(size_t)15));
+  const int nrows = item.v1 - item.v0;
 
   const TX* __restrict__ Xc = static_cast<const TX*>((t & 1) ? a.X1 : a.X0);
   TX* __restrict__ Xn = static_cast<TX*>((t & 1) ? a.X0 : a.X1);
@@ -290,6 +308,10 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
       for (int i = threadIdx.x; i < BW; i += blockDim.x) sZ[ng * BW + i] = 0u;
     }
     for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) s_cnt[i] = 0ull;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      const int v = a.g.order[item.v0 + i];
+      s_rows[i] = make_int4(v, a.g.row_ptr[v], a.g.row_ptr[v + 1], 0);
+    }
   }
   __syncthreads();
 
@@ -302,23 +324,45 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   const float thr = MIS ? 0.5f : 0.0f;
   const float lo = MIS ? 0.0f : -1.0f;
   const bool weighted = !MIS && a.g.w != nullptr;
-  const int32_t* __restrict__ rp = a.g.row_ptr;
   const int32_t* __restrict__ col = a.g.col;
   const int8_t* __restrict__ wts = a.g.w;
   constexpr int K = (LPR < 32 / VEC) ? LPR : 32 / VEC;  // lanes sharing one output word
   const unsigned rmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (sub * LPR));
   const unsigned char* sXl = smem + (DUP ? (sub & 1) * 64 : 0) + l * (VEC * (int)sizeof(TX));
 
-  bool stepping[VEC];
+  uint32_t stepm = 0u;  // bit e: trajectory b0 + e steps
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) stepping[e] = a.act ? (a.act[(int64_t)g * B + b0 + e] & ACT_STEP) != 0 : true;
+  for (int e = 0; e < VEC; ++e)
+    stepm |= (uint32_t)(a.act ? (a.act[(int64_t)g * B + b0 + e] & ACT_STEP) != 0 : true) << e;
+  // counts of nodes stay below 2^10 per lane (an item has at most 256 rows),
+  // so they are packed into one word per trajectory: MIS all three, MaxCut
+  // the last two (its first counter sums cut edges)
   int c0[VEC], c1[VEC], c2[VEC];
+  uint32_t cp[VEC];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
+  for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0, cp[e] = 0u;
 
-  for (int vb = item.v0 + warp * RPW; vb < item.v1; vb += nwarps * RPW) {
-    const int v = vb + sub;
-    const bool has = v < item.v1;
+  // column indices come in groups of four chunks; each group's loads are
+  // issued before the previous group is consumed (software pipeline), and a
+  // row's first group during the previous row's epilogue
+  int nxu[4], nxw[4];
+  auto first_group = [&](int i) {
+    const bool h = i < nrows;
+    const int4 r = s_rows[h ? i : 0];
+    const int rs_ = h ? r.y : 0, re_ = h ? r.z : 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = rs_ + c * LPR + l;
+      const bool jin = j < re_;
+      nxu[c] = jin ? __ldcs(col + j) - off : ng;
+      nxw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
+    }
+  };
+  first_group(warp * RPW + sub);
+  for (int vb = warp * RPW; vb < nrows; vb += nwarps * RPW) {
+    const bool has = vb + sub < nrows;
+    const int4 row = s_rows[has ? vb + sub : 0];
+    const int v = row.x;
     const int vl = has ? v - off : ng;
     const int64_t base = (int64_t)(has ? v : item.v0) * B + b0;
     const Pack<TX, VEC> xv = *reinterpret_cast<const Pack<TX, VEC>*>(sXl + (size_t)vl * pitch);
@@ -329,19 +373,9 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     uint32_t orw[4] = {0u, 0u, 0u, 0u};  // OR of the neighbours' words (BW <= 4)
 #pragma unroll
     for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
-    const int rs = has ? rp[v] : 0, re = has ? rp[v + 1] : 0;
+    const int rs = has ? row.y : 0, re = has ? row.z : 0;
     const int nch_w = __reduce_max_sync(0xffffffffu, (re - rs + LPR - 1) / LPR);
     int wsum = weighted ? 0 : re - rs;
-    // column indices come in groups of four chunks; the next group's loads
-    // are issued before the current group is consumed (software pipeline)
-    int nxu[4], nxw[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = rs + c * LPR + l;
-      const bool jin = j < re;
-      nxu[c] = jin ? __ldcs(col + j) - off : ng;
-      nxw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
-    }
     for (int ch0 = 0; ch0 < nch_w; ch0 += 4) {
       int myo[4], myw[4];
 #pragma unroll
@@ -377,15 +411,19 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
               pos[e] += (f[e] > thr) ? w : 0;
             }
           } else {
+            // two trajectories per packed add (IEEE round-to-nearest per
+            // element: the same sums as one scalar add each)
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-              acc[e] = acc[e] + f[e];
-              if (!MIS) pos[e] += (f[e] > thr);
+            for (int e = 0; e < VEC; e += 2) add_f32x2(acc[e], acc[e + 1], f[e], f[e + 1]);
+            if (!MIS) {
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) pos[e] += (f[e] > thr);
             }
           }
         }
       }
     }
+    first_group(vb + nwarps * RPW + sub);
     if (MIS) {
       for (int w = 0; w < BW; ++w)
         for (int o = 1; o < LPR; o <<= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
@@ -405,12 +443,16 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     for (int e = 0; e < VEC; ++e) {
       bool zn;
       int d0 = 0, d1 = 0, d2 = 0;
-      step_element<TX, TV>(a, MIS, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, stepping[e], xo.e[e], vo.e[e],
+      step_element<TX, TV>(a, MIS, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, (stepm >> e) & 1u, xo.e[e],
+                           vo.e[e],
                            zn, d0, d1, d2);
       if (has) {
-        c0[e] += d0;
-        c1[e] += d1;
-        c2[e] += d2;
+        if constexpr (MIS) {
+          cp[e] += (uint32_t)d0 | ((uint32_t)d1 << 10) | ((uint32_t)d2 << 20);
+        } else {
+          c0[e] += d0;
+          cp[e] += ((uint32_t)d1 << 10) | ((uint32_t)d2 << 20);
+        }
       }
       zbits |= (unsigned)zn << e;
     }
@@ -423,7 +465,13 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     for (int o = 1; o < K; o <<= 1) word |= __shfl_xor_sync(rmask, word, o);
     if (has && (l % K) == 0) Zn[(int64_t)v * BW + (b0 >> 5)] = word;
   }
-  flush_step_counters<VEC>(a, s_cnt, g, it, b0, c0, c1, c2, stepping);
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    if constexpr (MIS) c0[e] = (int)(cp[e] & 1023u);
+    c1[e] = (int)((cp[e] >> 10) & 1023u);
+    c2[e] = (int)(cp[e] >> 20);
+  }
+  flush_step_counters<VEC>(a, s_cnt, g, it, b0, LPR, c0, c1, c2, stepm);
 }
 
 size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng) {
@@ -432,11 +480,12 @@ size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng) {
   const size_t pitch = rowb == 64 ? 128 : rowb;
   const size_t xb = ((size_t)(max_ng + 1) * pitch + 15) & ~(size_t)15;
   const size_t zb = problem == PROB_MIS ? (((size_t)(max_ng + 1) * ((B + 31) / 32) * 4 + 15) & ~(size_t)15) : 0;
-  return xb + zb + 3 * (size_t)B * 8;
+  return xb + zb + ((3 * (size_t)B * 8 + 15) & ~(size_t)15) + (size_t)kItemMaxNodes * 16;
 }
 
 template <typename TX, typename TV, int VEC, int LPR, bool MIS, bool DUP>
 static cudaError_t launch_s(size_t smem, const StepArgs& a, int grid, cudaStream_t s) {
+  if (a.B != VEC * LPR) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_step_s<TX, TV, VEC, LPR, MIS, DUP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_step_s<TX, TV, VEC, LPR, MIS, DUP><<<grid, 512, smem, s>>>(a);
   return cudaGetLastError();
@@ -444,21 +493,55 @@ static cudaError_t launch_s(size_t smem, const StepArgs& a, int grid, cudaStream
 
 // lanes hold 8 bytes of x, or 16 when B/32 elements need more:
 // 2-byte x: B=32 -> (VEC 4, LPR 8, DUP), B=64 -> (4, 16), B=128 -> (4, 32);
-// 4-byte x: B=32 -> (2, 16), B=64 -> (2, 32), B=128 -> (4, 32)
+// 4-byte x: B=32 -> (2, 16), B=64 -> (2, 32), B=128 -> (4, 32).
+// Wide lanes (16 bytes, half the lanes per row, twice the rows per warp):
+// 2-byte x: B=32 -> (8, 4, DUP), B=64 -> (8, 8), B=128 -> (8, 16);
+// 4-byte x: B=32 -> (4, 8), B=64 -> (4, 16)
 template <typename TX, typename TV>
-static cudaError_t launch_smem(int B, size_t smem, bool mis, const StepArgs& a, int grid, cudaStream_t s) {
-  constexpr bool two = sizeof(TX) == 2;
-  if (mis) {
-    if (B == 32) return two ? launch_s<TX, TV, 4, 8, true, true>(smem, a, grid, s) : launch_s<TX, TV, 2, 16, true, false>(smem, a, grid, s);
-    if (B == 64) return two ? launch_s<TX, TV, 4, 16, true, false>(smem, a, grid, s) : launch_s<TX, TV, 2, 32, true, false>(smem, a, grid, s);
-    if (B == 128) return launch_s<TX, TV, 4, 32, true, false>(smem, a, grid, s);
+static cudaError_t launch_smem(int B, bool wide, size_t smem, bool mis, const StepArgs& a, int grid, cudaStream_t s) {
+  if constexpr (sizeof(TX) == 2) {
+    if (wide) {
+      if (mis) {
+        if (B == 32) return launch_s<TX, TV, 8, 4, true, true>(smem, a, grid, s);
+        if (B == 64) return launch_s<TX, TV, 8, 8, true, false>(smem, a, grid, s);
+        if (B == 128) return launch_s<TX, TV, 8, 16, true, false>(smem, a, grid, s);
+      } else {
+        if (B == 32) return launch_s<TX, TV, 8, 4, false, true>(smem, a, grid, s);
+        if (B == 64) return launch_s<TX, TV, 8, 8, false, false>(smem, a, grid, s);
+        if (B == 128) return launch_s<TX, TV, 8, 16, false, false>(smem, a, grid, s);
+      }
+    } else if (mis) {
+      if (B == 32) return launch_s<TX, TV, 4, 8, true, true>(smem, a, grid, s);
+      if (B == 64) return launch_s<TX, TV, 4, 16, true, false>(smem, a, grid, s);
+      if (B == 128) return launch_s<TX, TV, 4, 32, true, false>(smem, a, grid, s);
+    } else {
+      if (B == 32) return launch_s<TX, TV, 4, 8, false, true>(smem, a, grid, s);
+      if (B == 64) return launch_s<TX, TV, 4, 16, false, false>(smem, a, grid, s);
+      if (B == 128) return launch_s<TX, TV, 4, 32, false, false>(smem, a, grid, s);
+    }
   } else {
-    if (B == 32) return two ? launch_s<TX, TV, 4, 8, false, true>(smem, a, grid, s) : launch_s<TX, TV, 2, 16, false, false>(smem, a, grid, s);
-    if (B == 64) return two ? launch_s<TX, TV, 4, 16, false, false>(smem, a, grid, s) : launch_s<TX, TV, 2, 32, false, false>(smem, a, grid, s);
-    if (B == 128) return launch_s<TX, TV, 4, 32, false, false>(smem, a, grid, s);
+    if (wide) {
+      if (mis) {
+        if (B == 32) return launch_s<TX, TV, 4, 8, true, false>(smem, a, grid, s);
+        if (B == 64) return launch_s<TX, TV, 4, 16, true, false>(smem, a, grid, s);
+      } else {
+        if (B == 32) return launch_s<TX, TV, 4, 8, false, false>(smem, a, grid, s);
+        if (B == 64) return launch_s<TX, TV, 4, 16, false, false>(smem, a, grid, s);
+      }
+    } else if (mis) {
+      if (B == 32) return launch_s<TX, TV, 2, 16, true, false>(smem, a, grid, s);
+      if (B == 64) return launch_s<TX, TV, 2, 32, true, false>(smem, a, grid, s);
+      if (B == 128) return launch_s<TX, TV, 4, 32, true, false>(smem, a, grid, s);
+    } else {
+      if (B == 32) return launch_s<TX, TV, 2, 16, false, false>(smem, a, grid, s);
+      if (B == 64) return launch_s<TX, TV, 2, 32, false, false>(smem, a, grid, s);
+      if (B == 128) return launch_s<TX, TV, 4, 32, false, false>(smem, a, grid, s);
+    }
   }
   return cudaErrorInvalidValue;
 }
+
+bool step_wide_possible(int B, int x_dtype) { return x_dtype != DT_F32 ? (B == 32 || B == 64 || B == 128) : (B == 32 || B == 64); }
 
 template <typename TX, typename TV, int VEC>
 static cudaError_t launch_vec(const StepArgs& a, int grid, cudaStream_t s) {
@@ -467,9 +550,9 @@ static cudaError_t launch_vec(const StepArgs& a, int grid, cudaStream_t s) {
 }
 
 template <typename TX, typename TV>
-static cudaError_t launch_tv(int vec, bool smem_path, size_t smem, bool mis, const StepArgs& a, int grid,
-                             cudaStream_t s) {
-  if (smem_path) return launch_smem<TX, TV>(a.B, smem, mis, a, grid, s);
+static cudaError_t launch_tv(int vec, bool smem_path, bool wide, size_t smem, bool mis, const StepArgs& a,
+                             int grid, cudaStream_t s) {
+  if (smem_path) return launch_smem<TX, TV>(a.B, wide, smem, mis, a, grid, s);
   switch (vec) {
     case 1: return launch_vec<TX, TV, 1>(a, grid, s);
     case 2: return launch_vec<TX, TV, 2>(a, grid, s);
@@ -499,16 +582,17 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   a.act = act;
   a.gflag_step = gflag_step;
   a.tick = S.tick;
-  const int vec = S.B >= 32 ? S.B / 32 : 1;
+  const int vec = S.step_vec > 0 ? S.step_vec : (S.B >= 32 ? S.B / 32 : 1);
   const bool sp = smem > 0;
+  const bool wide = S.step_wide != 0;
   const bool mis = S.p.problem == PROB_MIS;
   const int grid = S.g.num_items;
   const int xd = S.p.x_dtype, vd = S.p.v_dtype;
-  if (xd == DT_F32) return launch_tv<float, float>(vec, sp, smem, mis, a, grid, stream);
-  if (xd == DT_BF16 && vd == DT_BF16) return launch_tv<__nv_bfloat16, __nv_bfloat16>(vec, sp, smem, mis, a, grid, stream);
-  if (xd == DT_BF16 && vd == DT_F32) return launch_tv<__nv_bfloat16, float>(vec, sp, smem, mis, a, grid, stream);
-  if (xd == DT_F16 && vd == DT_F16) return launch_tv<__half, __half>(vec, sp, smem, mis, a, grid, stream);
-  if (xd == DT_F16 && vd == DT_F32) return launch_tv<__half, float>(vec, sp, smem, mis, a, grid, stream);
+  if (xd == DT_F32) return launch_tv<float, float>(vec, sp, wide, smem, mis, a, grid, stream);
+  if (xd == DT_BF16 && vd == DT_BF16) return launch_tv<__nv_bfloat16, __nv_bfloat16>(vec, sp, wide, smem, mis, a, grid, stream);
+  if (xd == DT_BF16 && vd == DT_F32) return launch_tv<__nv_bfloat16, float>(vec, sp, wide, smem, mis, a, grid, stream);
+  if (xd == DT_F16 && vd == DT_F16) return launch_tv<__half, __half>(vec, sp, wide, smem, mis, a, grid, stream);
+  if (xd == DT_F16 && vd == DT_F32) return launch_tv<__half, float>(vec, sp, wide, smem, mis, a, grid, stream);
   return cudaErrorInvalidValue;
 }
 

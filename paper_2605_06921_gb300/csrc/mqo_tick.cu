@@ -201,6 +201,7 @@ __global__ void k_ctrl(CtrlArgs A) {
   S.st[tau] = st;
   S.act[tau] = act;
   S.rnd[tau] = round;
+  S.bestv[tau] = st.best;
   const int32_t stamp = (int32_t)(t + 1);
   const int G = S.g.num_graphs;
   if (act & ACT_APPLY_MASK) {
@@ -743,18 +744,19 @@ cudaError_t launch_objective(const SolverDev& S, double* out, cudaStream_t strea
 }
 
 // after a standalone local search: restore the machine state, keep best
-__global__ void k_ls_merge(TrajState* st, const TrajState* saved, int64_t T) {
+__global__ void k_ls_merge(TrajState* st, const TrajState* saved, int64_t* bestv, int64_t T) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= T) return;
   TrajState s = saved[i];
   s.best = st[i].best;
   s.accepts = st[i].accepts;
   st[i] = s;
+  bestv[i] = s.best;
 }
 
 cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStream_t stream) {
   const int64_t T = (int64_t)S.g.num_graphs * S.B;
-  k_ls_merge<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(S.st, saved, T);
+  k_ls_merge<<<(unsigned)((T + 255) / 256), 256, 0, stream>>>(S.st, saved, S.bestv, T);
   return cudaGetLastError();
 }
 
@@ -784,6 +786,7 @@ __global__ void k_state_init(SolverDev S) {
     S.st[tau] = st;
     S.act[tau] = ACT_INIT;
     S.rnd[tau] = RD_NONE;
+    S.bestv[tau] = st.best;
     for (int r = 0; r < S.R; ++r) S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
     const int g = (int)(tau / S.B);
     S.gflag[g] = (int32_t)(t + 1);

@@ -143,6 +143,20 @@ def test_generic_step_kernel_on_small_graphs(mq, monkeypatch, problem, B, xd):
     _machine(mq, G, mq.params(problem=problem, batch=B, x_dtype=xd, t_gs=3, descent_cap=20, seed=3), 150)
 
 
+@pytest.mark.parametrize("problem", [0, 1])
+@pytest.mark.parametrize("B,xd,vd", [(32, 1, 1), (32, 2, 0), (32, 0, 0), (64, 1, 1), (64, 0, 0), (128, 2, 2)])
+def test_wide_lane_step_kernel(mq, monkeypatch, problem, B, xd, vd):
+    """the shared-memory step kernel with 16-byte lanes (an autotuner plan)"""
+    monkeypatch.setenv("MQO_STEP_KERNEL", "wide")
+    p = mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, alpha=0.8 if problem == 0 else 0.05,
+                  momentum=0.5, seed=B + 7)
+    _plain_steps(mq, small_batch(3, seed=B + 2), p, 8)
+    G = small_batch(2, 30, 60, 0.15, seed=B + 5)
+    s, _ = _machine(mq, G, mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, t_gs=3, descent_cap=20,
+                                     seed=5), 150)
+    assert s.info()["step_kernel"] == "smem_wide"
+
+
 @pytest.mark.parametrize("xd,vd", [(1, 1), (1, 0), (2, 2), (2, 0)])
 @pytest.mark.parametrize("B", [16, 32, 128])
 def test_plain_steps_low_precision_mis(mq, xd, vd, B):
@@ -191,7 +205,7 @@ def test_evaluate_bitexact(mq, problem, weighted, B):
 
 
 # ------------------------------------------------------------------ the machine
-def _machine(mq, G, p, nticks, trace=0):
+def _machine(mq, G, p, nticks, trace=0, tune_at=None):
     s = mq.Solver(mq.Graph(G), p)
     po = okw(p)
     B = p.batch
@@ -207,7 +221,14 @@ def _machine(mq, G, p, nticks, trace=0):
                 tr.run(1)
                 if tr.state["phase"] == oracle.PH_DESCENT and tr.state["last_round"] == -1:
                     assert close(gx[lo:hi, b], tr.x), (k, g, b)
-    s.run(nticks - trace)
+    if tune_at is None:
+        s.run(nticks - trace)
+    else:
+        s.run(tune_at - trace)
+        plan = s.autotune(ticks=5)
+        assert plan["ms_per_tick"] > 0
+        assert plan["step_kernel"].startswith("smem") == (plan["lanes_vec"] == 0)
+        s.run(nticks - tune_at)
     vals, bits = s.best()
     z = mq.unpack_bits(bits, G.n, B)
     states = s.traj_state()
@@ -241,6 +262,18 @@ def test_machine_packed_mis(mq, B):
     G = small_batch(4, 30, 70, 0.15, seed=B)
     p = mq.params(batch=B, alpha=0.8, momentum=0.45, rho=0.6, t_gs=4, descent_cap=25, seed=B)
     _machine(mq, G, p, 400, trace=30)
+
+
+@pytest.mark.parametrize("problem", [0, 1])
+def test_autotune_keeps_results(mq, problem):
+    """Autotuning mid-run (every plan tried, state restored) changes no tick of the machine."""
+    G = small_batch(4, 60, 120, 0.1, seed=11)
+    if problem == 0:
+        p = mq.params(batch=32, alpha=0.8, momentum=0.45, rho=0.6, t_gs=4, descent_cap=25, seed=3)
+    else:
+        p = mq.params(problem=1, batch=32, alpha=0.05, momentum=0.8, lambda_=0.001, rho=0.8, t_gs=3,
+                      descent_cap=40, init_kind=1, sigma=0.2, seed=3)
+    _machine(mq, G, p, 200, trace=0, tune_at=60)
 
 
 def test_machine_mis_low_precision(mq):
