@@ -27,7 +27,8 @@ _lib = None
 
 MIS, MAXCUT = 0, 1
 F32, BF16, F16 = 0, 1, 2
-PH_DESCENT, PH_REPAIR, PH_LS = 0, 1, 2
+PH_DESCENT, PH_REPAIR, PH_LS, PH_WAIT = 0, 1, 2, 3
+EP_DESCENT, EP_LS = 0, 1
 INT64_MIN = -(1 << 63)
 
 
@@ -53,7 +54,15 @@ class OrcParams(C.Structure):
         ("alpha", C.c_float), ("momentum", C.c_float), ("gamma", C.c_float), ("lambda_", C.c_float),
         ("rho", C.c_double), ("sigma", C.c_float), ("t_gs", C.c_int32), ("descent_cap", C.c_int32),
         ("init_kind", C.c_int32), ("local_search", C.c_int32), ("repair", C.c_int32), ("seed", C.c_uint64),
+        ("pool_k", C.c_int32), ("pad0", C.c_int32),
     ]
+
+
+class OrcPool(C.Structure):
+    _fields_ = [("epoch", C.c_int32), ("count", C.c_int32), ("best", C.c_int64), ("merges", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class OrcState(C.Structure):
@@ -61,7 +70,7 @@ class OrcState(C.Structure):
         ("phase", C.c_int32), ("s", C.c_int32), ("r", C.c_int32), ("o", C.c_int32),
         ("best", C.c_int64), ("ticks", C.c_int64), ("last_round", C.c_int32), ("last_commits", C.c_int64),
         ("ev_value", C.c_int64), ("ev_a", C.c_int64), ("ev_b", C.c_int64),
-        ("accepts", C.c_int64), ("descents", C.c_int64),
+        ("accepts", C.c_int64), ("descents", C.c_int64), ("held", C.c_int64),
     ]
 
     def as_dict(self):
@@ -95,6 +104,10 @@ def lib():
             _lib.orc_state_init.argtypes = [P]
             _lib.orc_run_trajectory.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, P, P, P, P, P, P, P,
                                                 C.c_int64]
+            _lib.orc_pool_pick.restype = C.c_int64
+            _lib.orc_pool_pick.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_int64]
+            _lib.orc_run_pool.argtypes = [P, P, C.c_int64, C.c_int32, C.c_int64, C.c_int32, P, P, P, P, P, P, P,
+                                          P, P]
             _lib.orc_objective_f64.restype = C.c_double
             _lib.orc_objective_f64.argtypes = [P, C.c_int32, C.c_double, C.c_double, P]
             _lib.orc_gradient_f64.argtypes = [P, C.c_int32, C.c_double, C.c_double, P, P]
@@ -126,9 +139,9 @@ class Graph:
 
 def params(problem=MIS, batch=1, x_dtype=F32, v_dtype=F32, alpha=0.8, momentum=0.3, gamma=2.0,
            lambda_=0.001, rho=0.7, sigma=0.1, t_gs=60, descent_cap=50, init_kind=0, local_search=1,
-           repair=1, seed=0):
+           repair=1, seed=0, pool_k=0):
     return OrcParams(problem, batch, x_dtype, v_dtype, alpha, momentum, gamma, lambda_, rho, sigma, t_gs,
-                     descent_cap, init_kind, local_search, repair, seed)
+                     descent_cap, init_kind, local_search, repair, seed, pool_k, 0)
 
 
 def philox4x64_10(ctr, key):
@@ -254,6 +267,43 @@ class Trajectory:
     @property
     def state(self):
         return self.st.as_dict()
+
+
+def pool_pick(seed, traj, outer, rnd, count):
+    return int(lib().orc_pool_pick(seed, traj, outer, rnd, count))
+
+
+class PoolGraph:
+    """The B trajectories of one graph in pool mode (pmQO, Alg. 3/4);
+    trajectory ids traj0 .. traj0+B-1; ``run(k)`` advances them k ticks."""
+
+    def __init__(self, g: Graph, p, traj0: int, B: int):
+        self.g, self.p, self.traj0, self.B = g, p, int(traj0), int(B)
+        n, K = g.n, max(1, int(p.pool_k))
+        self.st = (OrcState * B)()
+        self.x = np.zeros((B, n), dtype=np.float32)
+        self.V = np.zeros((B, n), dtype=np.float32)
+        self.zbest = np.zeros((B, n), dtype=np.uint8)
+        self.zwork = np.zeros((B, n), dtype=np.uint8)
+        self.zx_prev = np.zeros((B, n), dtype=np.uint8)
+        self.pool = OrcPool()
+        self.pool_bits = np.zeros((K, n), dtype=np.uint8)
+        self.pool_vals = np.zeros(K, dtype=np.int64)
+        self.started = False
+
+    def run(self, nticks: int):
+        lib().orc_run_pool(self.g.ref(), C.byref(self.p), self.traj0, self.B, int(nticks), int(self.started),
+                           self.st, _ptr(self.x), _ptr(self.V), _ptr(self.zbest), _ptr(self.zwork),
+                           _ptr(self.zx_prev), C.byref(self.pool), _ptr(self.pool_bits), _ptr(self.pool_vals))
+        self.started = True
+
+    def state(self, b):
+        return self.st[b].as_dict()
+
+    def members(self):
+        """(values, bits) of the pool members, best first"""
+        c = self.pool.count
+        return self.pool_vals[:c].copy(), self.pool_bits[:c].copy()
 
 
 def objective_f64(g: Graph, problem, gamma, lambda_, x):

@@ -35,7 +35,7 @@
 
 enum { ORC_MIS = 0, ORC_MAXCUT = 1 };
 enum { ORC_F32 = 0, ORC_BF16 = 1, ORC_F16 = 2 };
-enum { ORC_PH_DESCENT = 0, ORC_PH_REPAIR = 1, ORC_PH_LS = 2 };
+enum { ORC_PH_DESCENT = 0, ORC_PH_REPAIR = 1, ORC_PH_LS = 2, ORC_PH_WAIT = 3 };
 enum {
   ORC_R_NONE = -1,
   ORC_R_COUNT = 0,
@@ -70,6 +70,8 @@ typedef struct {
   int32_t local_search;
   int32_t repair;
   uint64_t seed;
+  int32_t pool_k;     /* 0: independent trajectories (Alg. 1/2); K >= 1: pmQO pool (Alg. 3/4) */
+  int32_t pad0;
 } orc_params;
 
 /* Per-trajectory machine state, mirrored field by field for the tests. */
@@ -88,6 +90,7 @@ typedef struct {
   int64_t ev_b;       /* MIS: uncovered (free) nodes; MaxCut: 1-flip candidates */
   int64_t accepts;
   int64_t descents;
+  int64_t held;       /* pool mode: value of the set held while waiting, INT64_MIN if none */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -125,6 +128,7 @@ ORC_API void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2
 /* key = (seed, trajectory id); ctr = (tag, outer iteration, a, b).      */
 #define ORC_TAG_INIT 1ULL
 #define ORC_TAG_RESET 2ULL
+#define ORC_TAG_POOL 3ULL
 
 /* top 24 bits of a 64-bit word as an exact float in [0,1) */
 static float u24(uint64_t w) { return (float)(w >> 40) * (1.0f / 16777216.0f); }
@@ -679,21 +683,24 @@ static void start_outer(orc_traj* T) {
   for (int64_t v = 0; v < T->g->n; ++v) T->V[v] = 0.0f;
 }
 
-static void reset_from_best(orc_traj* T) {
-  /* Alg. 1 steps 6-8 / Alg. 2 steps 6-8: x from the best set, then the
-   * coordinates in R are set to 0; the momentum starts from zero. */
+static void reset_from(orc_traj* T, const uint8_t* base) {
+  /* Alg. 1 steps 6-8 / Alg. 2 steps 6-8: x from the base set (the best
+   * set; a pool member in Alg. 3/4 step 7), then the coordinates in R are
+   * set to 0; the momentum starts from zero. */
   const orc_params* p = T->p;
   orc_state* st = T->st;
   orc_reset_mask(T->g->n, p->rho, p->seed, T->traj, st->o, st->r, T->in_r);
   for (int64_t v = 0; v < T->g->n; ++v) {
     float val;
-    if (p->problem == ORC_MIS) val = T->zbest[v] ? 1.0f : 0.0f;
-    else val = T->zbest[v] ? 1.0f : -1.0f;
+    if (p->problem == ORC_MIS) val = base[v] ? 1.0f : 0.0f;
+    else val = base[v] ? 1.0f : -1.0f;
     if (T->in_r[v]) val = 0.0f;
     T->x[v] = val;
     T->V[v] = 0.0f;
   }
 }
+
+static void reset_from_best(orc_traj* T) { reset_from(T, T->zbest); }
 
 /* returns the discrete round to run in this tick, or ORC_R_NONE */
 static int after_accept(orc_traj* T) {
@@ -807,6 +814,7 @@ ORC_API void orc_state_init(orc_state* st) {
   st->phase = ORC_PH_DESCENT;
   st->best = INT64_MIN;
   st->last_round = ORC_R_NONE;
+  st->held = INT64_MIN;
 }
 
 /* Run one trajectory for `nticks` ticks from a fresh start (outer
@@ -834,6 +842,260 @@ ORC_API void orc_run_trajectory(const orc_graph* g, const orc_params* p, int64_t
     if (trace_x && t < trace_ticks) memcpy(trace_x + t * n, x, (size_t)n * sizeof(float));
   }
   free(T.xn); free(T.Vn); free(T.in_r);
+}
+
+/* ------------------------------------------------------------------ */
+/* pmQO: Alg. 3 (MIS) and Alg. 4 (MaxCut).  The B trajectories of one   */
+/* graph share a pool P_K of the K best sets found so far.  A round runs */
+/* every trajectory to the end of its descent (and the repair of a      */
+/* capped MIS descent); a trajectory whose descent is over holds its set */
+/* and waits.  When all B wait, the graph merges them into the pool      */
+/* (steps 4 and 11: P_K <- TopK(P_K U batch)), takes the best set from   */
+/* the pool (steps 5 and 12), and then either starts the next round --   */
+/* each trajectory draws its base set uniformly from the pool (step 7),  */
+/* zeroes its reset set R (steps 8-9) and descends again (step 10) -- or */
+/* after T_gs rounds runs local search (step 13: OneTwoSwap on the best  */
+/* set for MIS, OneTwoFlip on every pool member for MaxCut), and then a  */
+/* new outer iteration with fresh initialisations (step 2).  The pool     */
+/* persists across outer iterations.  Ties in TopK keep the earlier      */
+/* candidate (pool members in pool order, then the batch in trajectory   */
+/* order).  Every trajectory's best set is the graph's best set.         */
+/* ------------------------------------------------------------------ */
+enum { ORC_EP_DESCENT = 0, ORC_EP_LS = 1 };
+enum { ORC_DEC_NONE = 0, ORC_DEC_NEXT = 1, ORC_DEC_LS = 2, ORC_DEC_OUTER = 3 };
+
+typedef struct {
+  int32_t epoch;  /* ORC_EP_*: what the trajectories are finishing */
+  int32_t count;  /* pool members (<= K) */
+  int64_t best;   /* value of the graph's best set, INT64_MIN before the first */
+  int64_t merges; /* pool merges so far */
+} orc_pool;
+
+/* Step 7: a pool index uniform in [0, count): the high word of u * count
+ * for a 64-bit Philox word u keyed like the other draws. */
+ORC_API int64_t orc_pool_pick(uint64_t seed, int64_t traj, int64_t outer, int64_t round, int64_t count) {
+  if (count <= 0) return -1;
+  uint64_t key[2] = {seed, (uint64_t)traj};
+  uint64_t ctr[4] = {ORC_TAG_POOL, (uint64_t)outer, (uint64_t)round, 0};
+  uint64_t r[4], hi, lo;
+  orc_philox4x64_10(ctr, key, r);
+  mul128(r[0], (uint64_t)count, &hi, &lo);
+  return (int64_t)hi;
+}
+
+static void hold(orc_traj* T, const uint8_t* src, int64_t value) {
+  if (src != T->zwork) memcpy(T->zwork, src, (size_t)T->g->n);
+  T->st->held = value;
+  T->st->phase = ORC_PH_WAIT;
+}
+
+/* one tick of one trajectory in pool mode; dec is the graph's decision
+ * of this tick, base the set to reset from (NEXT) or to search from (LS,
+ * when ls_me) */
+static void tick_pool(orc_traj* T, int dec, const uint8_t* base, int ls_me) {
+  orc_state* st = T->st;
+  const orc_params* p = T->p;
+  const int64_t n = T->g->n;
+  int mis = p->problem == ORC_MIS;
+  int round = ORC_R_NONE;
+
+  if (st->phase == ORC_PH_WAIT) {
+    if (dec == ORC_DEC_NEXT) {
+      st->r += 1;
+      st->s = 0;
+      st->phase = ORC_PH_DESCENT;
+      reset_from(T, base);
+    } else if (dec == ORC_DEC_LS) {
+      st->held = INT64_MIN;
+      if (ls_me) {
+        st->phase = ORC_PH_LS;
+        memcpy(T->zwork, base, (size_t)n);
+        round = ORC_R_COUNT;
+      }
+    } else if (dec == ORC_DEC_OUTER) {
+      st->held = INT64_MIN;
+      start_outer(T);
+    }
+  } else if (st->phase == ORC_PH_DESCENT) {
+    if (st->s > 0) {
+      int pass = mis ? (st->ev_a == 0 && st->ev_b == 0) : (st->ev_a == 0);
+      if (pass) {
+        st->descents += 1;
+        hold(T, T->zx_prev, st->ev_value);
+      } else if (st->s >= p->descent_cap) {
+        st->descents += 1;
+        if (mis && p->repair) {
+          st->phase = ORC_PH_REPAIR;
+          memcpy(T->zwork, T->zx_prev, (size_t)n);
+          round = ORC_R_COUNT;
+        } else {
+          /* an unrepaired capped MIS point is not a candidate */
+          hold(T, T->zx_prev, mis ? INT64_MIN : st->ev_value);
+        }
+      }
+    }
+  } else if (st->phase == ORC_PH_REPAIR) {
+    if (st->ev_a > 0) round = ORC_R_DROP;
+    else if (st->ev_b > 0) round = ORC_R_COMPLETE;
+    else hold(T, T->zwork, st->ev_value);
+  } else { /* local search */
+    int done;
+    if (mis) {
+      if (st->ev_b > 0) { round = ORC_R_COMPLETE; done = 0; }
+      else if (!(st->last_round == ORC_R_SWAP && st->last_commits == 0)) { round = ORC_R_SWAP; done = 0; }
+      else done = 1;
+    } else {
+      if (st->ev_b > 0) { round = ORC_R_FLIP1; done = 0; }
+      else if (!(st->last_round == ORC_R_FLIP2 && st->last_commits == 0)) { round = ORC_R_FLIP2; done = 0; }
+      else done = 1;
+    }
+    if (done) hold(T, T->zwork, st->ev_value);
+  }
+
+  if (st->phase == ORC_PH_DESCENT) {
+    int64_t ev[4];
+    orc_descent_step(T->g, p, T->x, T->V, T->xn, T->Vn, T->zx_prev, ev);
+    memcpy(T->x, T->xn, (size_t)n * sizeof(float));
+    memcpy(T->V, T->Vn, (size_t)n * sizeof(float));
+    st->ev_value = ev[0]; st->ev_a = ev[1]; st->ev_b = ev[2];
+    st->s += 1;
+    st->last_round = ORC_R_NONE;
+    st->last_commits = 0;
+  } else if (round != ORC_R_NONE) {
+    int64_t k = run_round(T, round);
+    disc_counts(T->g, p, T->zwork, st);
+    st->last_round = round;
+    st->last_commits = k;
+  }
+  /* a waiting trajectory does nothing this tick */
+  st->ticks += 1;
+}
+
+static void set_best_all(orc_traj* T, int B, orc_pool* P, int64_t value, const uint8_t* bits) {
+  P->best = value;
+  for (int b = 0; b < B; ++b) {
+    if (T[b].zbest != bits) memcpy(T[b].zbest, bits, (size_t)T[b].g->n);
+    T[b].st->best = value;
+    T[b].st->accepts += 1;
+  }
+}
+
+/* The graph's step at the start of a tick, on the states left by the
+ * previous tick.  Returns the decision and fills base[b] / ls[b]. */
+static int pool_control(orc_traj* T, int B, orc_pool* P, uint8_t* pool_bits, int64_t* pool_vals, uint8_t* tmp,
+                        const uint8_t* zero, const uint8_t** base, int* ls) {
+  const orc_params* p = T[0].p;
+  const int64_t n = T[0].g->n;
+  const int K = p->pool_k;
+  for (int b = 0; b < B; ++b) {
+    base[b] = zero;
+    ls[b] = 0;
+    if (T[b].st->phase != ORC_PH_WAIT) return ORC_DEC_NONE;
+  }
+  if (P->epoch == ORC_EP_LS) {
+    /* end of step 13: the best set takes the best search result */
+    int win = -1;
+    int64_t bv = P->best;
+    for (int b = 0; b < B; ++b)
+      if (T[b].st->held != INT64_MIN && T[b].st->held > bv) { bv = T[b].st->held; win = b; }
+    if (win >= 0) {
+      memcpy(tmp, T[win].zwork, (size_t)n);
+      set_best_all(T, B, P, bv, tmp);
+    }
+    P->epoch = ORC_EP_DESCENT;
+    return ORC_DEC_OUTER;
+  }
+  /* steps 4 / 11: candidates = pool members (pool order), then the held
+   * sets (trajectory order); stable selection of the K largest values */
+  int nc = 0;
+  int64_t* cv = malloc(sizeof(int64_t) * (size_t)(K + B));
+  int* cs = malloc(sizeof(int) * (size_t)(K + B));
+  for (int j = 0; j < P->count; ++j) { cv[nc] = pool_vals[j]; cs[nc] = j; ++nc; }
+  for (int b = 0; b < B; ++b)
+    if (T[b].st->held != INT64_MIN) { cv[nc] = T[b].st->held; cs[nc] = K + b; ++nc; }
+  for (int i = 1; i < nc; ++i) { /* insertion sort, descending, stable */
+    int64_t v = cv[i];
+    int c = cs[i], j = i - 1;
+    while (j >= 0 && cv[j] < v) { cv[j + 1] = cv[j]; cs[j + 1] = cs[j]; --j; }
+    cv[j + 1] = v;
+    cs[j + 1] = c;
+  }
+  int keep = nc < K ? nc : K;
+  uint8_t* newbits = malloc((size_t)K * (size_t)n + 1);
+  for (int s = 0; s < keep; ++s) {
+    const uint8_t* src = cs[s] < K ? pool_bits + (size_t)cs[s] * (size_t)n : T[cs[s] - K].zwork;
+    memcpy(newbits + (size_t)s * (size_t)n, src, (size_t)n);
+  }
+  memcpy(pool_bits, newbits, (size_t)keep * (size_t)n);
+  for (int s = 0; s < keep; ++s) pool_vals[s] = cv[s];
+  P->count = keep;
+  P->merges += 1;
+  free(newbits); free(cv); free(cs);
+  /* steps 5 / 12 */
+  if (P->count > 0 && pool_vals[0] > P->best) set_best_all(T, B, P, pool_vals[0], pool_bits);
+  const orc_state* s0 = T[0].st;
+  if (s0->r < p->t_gs) {
+    for (int b = 0; b < B; ++b) {
+      int64_t k = orc_pool_pick(p->seed, T[b].traj, s0->o, s0->r + 1, P->count);
+      base[b] = k >= 0 ? pool_bits + (size_t)k * (size_t)n : zero;
+    }
+    return ORC_DEC_NEXT;
+  }
+  if (p->local_search) {
+    P->epoch = ORC_EP_LS;
+    for (int b = 0; b < B; ++b) {
+      if (p->problem == ORC_MIS) {
+        ls[b] = b == 0;
+        base[b] = T[0].zbest;
+      } else {
+        ls[b] = b < P->count;
+        base[b] = b < P->count ? pool_bits + (size_t)b * (size_t)n : zero;
+      }
+    }
+    return ORC_DEC_LS;
+  }
+  return ORC_DEC_OUTER;
+}
+
+/* Run the B trajectories traj0 .. traj0+B-1 of one graph in pool mode for
+ * nticks ticks, from a fresh start or (resume) from the state passed in.
+ * st: B states; x, V: B*n floats; zbest, zwork, zx_prev: B*n bytes;
+ * pool_bits: K*n bytes; pool_vals: K values. */
+ORC_API void orc_run_pool(const orc_graph* g, const orc_params* p, int64_t traj0, int32_t B, int64_t nticks,
+                          int32_t resume, orc_state* st, float* x, float* V, uint8_t* zbest, uint8_t* zwork,
+                          uint8_t* zx_prev, orc_pool* P, uint8_t* pool_bits, int64_t* pool_vals) {
+  const int64_t n = g->n;
+  orc_traj* T = calloc((size_t)B, sizeof(orc_traj));
+  const uint8_t** base = calloc((size_t)B, sizeof(uint8_t*));
+  int* ls = calloc((size_t)B, sizeof(int));
+  uint8_t* zero = calloc((size_t)n + 1, 1);
+  uint8_t* tmp = malloc((size_t)n + 1);
+  for (int b = 0; b < B; ++b) {
+    T[b].g = g; T[b].p = p; T[b].traj = traj0 + b; T[b].st = st + b;
+    T[b].x = x + (size_t)b * (size_t)n; T[b].V = V + (size_t)b * (size_t)n;
+    T[b].zbest = zbest + (size_t)b * (size_t)n; T[b].zwork = zwork + (size_t)b * (size_t)n;
+    T[b].zx_prev = zx_prev + (size_t)b * (size_t)n;
+    T[b].xn = malloc(((size_t)n + 1) * sizeof(float));
+    T[b].Vn = malloc(((size_t)n + 1) * sizeof(float));
+    T[b].in_r = malloc((size_t)n + 1);
+    if (!resume) {
+      orc_state_init(T[b].st);
+      orc_init_x(g, p, T[b].traj, 0, T[b].x);
+      for (int64_t v = 0; v < n; ++v) { T[b].V[v] = 0.0f; T[b].zbest[v] = 0; T[b].zwork[v] = 0; T[b].zx_prev[v] = 0; }
+    }
+  }
+  if (!resume) {
+    P->epoch = ORC_EP_DESCENT;
+    P->count = 0;
+    P->best = INT64_MIN;
+    P->merges = 0;
+  }
+  for (int64_t t = 0; t < nticks; ++t) {
+    int dec = pool_control(T, B, P, pool_bits, pool_vals, tmp, zero, base, ls);
+    for (int b = 0; b < B; ++b) tick_pool(&T[b], dec, base[b], ls[b]);
+  }
+  for (int b = 0; b < B; ++b) { free(T[b].xn); free(T[b].Vn); free(T[b].in_r); }
+  free(T); free(base); free(ls); free(zero); free(tmp);
 }
 
 /* ------------------------------------------------------------------ */
