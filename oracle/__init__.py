@@ -26,6 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 MIS, MAXCUT = 0, 1
+F_B, F_L, F_P, F_A = 0, 1, 2, 3  # MaxCut relaxations
 F32, BF16, F16 = 0, 1, 2
 PH_DESCENT, PH_REPAIR, PH_LS, PH_WAIT = 0, 1, 2, 3
 EP_DESCENT, EP_LS = 0, 1
@@ -54,7 +55,7 @@ class OrcParams(C.Structure):
         ("alpha", C.c_float), ("momentum", C.c_float), ("gamma", C.c_float), ("lambda_", C.c_float),
         ("rho", C.c_double), ("sigma", C.c_float), ("t_gs", C.c_int32), ("descent_cap", C.c_int32),
         ("init_kind", C.c_int32), ("local_search", C.c_int32), ("repair", C.c_int32), ("seed", C.c_uint64),
-        ("pool_k", C.c_int32), ("pad0", C.c_int32),
+        ("pool_k", C.c_int32), ("objective", C.c_int32),
     ]
 
 
@@ -108,6 +109,10 @@ def lib():
             _lib.orc_pool_pick.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_int64]
             _lib.orc_run_pool.argtypes = [P, P, C.c_int64, C.c_int32, C.c_int64, C.c_int32, P, P, P, P, P, P, P,
                                           P, P]
+            _lib.orc_eval_cut_obj.argtypes = [P, P, C.c_int32, C.c_float, P]
+            _lib.orc_cut_objective_f64.restype = C.c_double
+            _lib.orc_cut_objective_f64.argtypes = [P, C.c_int32, C.c_double, P]
+            _lib.orc_cut_gradient_f64.argtypes = [P, C.c_int32, C.c_double, P, P]
             _lib.orc_objective_f64.restype = C.c_double
             _lib.orc_objective_f64.argtypes = [P, C.c_int32, C.c_double, C.c_double, P]
             _lib.orc_gradient_f64.argtypes = [P, C.c_int32, C.c_double, C.c_double, P, P]
@@ -139,9 +144,9 @@ class Graph:
 
 def params(problem=MIS, batch=1, x_dtype=F32, v_dtype=F32, alpha=0.8, momentum=0.3, gamma=2.0,
            lambda_=0.001, rho=0.7, sigma=0.1, t_gs=60, descent_cap=50, init_kind=0, local_search=1,
-           repair=1, seed=0, pool_k=0):
+           repair=1, seed=0, pool_k=0, objective=0):
     return OrcParams(problem, batch, x_dtype, v_dtype, alpha, momentum, gamma, lambda_, rho, sigma, t_gs,
-                     descent_cap, init_kind, local_search, repair, seed, pool_k, 0)
+                     descent_cap, init_kind, local_search, repair, seed, pool_k, objective)
 
 
 def philox4x64_10(ctr, key):
@@ -193,6 +198,26 @@ def eval_cut(g: Graph, z):
     out = np.zeros(4, dtype=np.int64)
     lib().orc_eval_cut(g.ref(), _ptr(z), _ptr(out))
     return tuple(int(v) for v in out[:3])
+
+
+def eval_cut_obj(g: Graph, z, objective, lambda_):
+    """(cut, nodes not fixed under the relaxation's PGA, 1-flip candidates)"""
+    z = np.ascontiguousarray(z, dtype=np.uint8)
+    out = np.zeros(4, dtype=np.int64)
+    lib().orc_eval_cut_obj(g.ref(), _ptr(z), int(objective), float(lambda_), _ptr(out))
+    return tuple(int(v) for v in out[:3])
+
+
+def cut_objective_f64(g: Graph, objective, lambda_, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_cut_objective_f64(g.ref(), int(objective), float(lambda_), _ptr(x))
+
+
+def cut_gradient_f64(g: Graph, objective, lambda_, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(g.n, dtype=np.float64)
+    lib().orc_cut_gradient_f64(g.ref(), int(objective), float(lambda_), _ptr(x), _ptr(out))
+    return out
 
 
 def descent_step(g: Graph, p, x, V):

@@ -34,6 +34,7 @@
 #define ORC_API __attribute__((visibility("default")))
 
 enum { ORC_MIS = 0, ORC_MAXCUT = 1 };
+enum { ORC_F_B = 0, ORC_F_L = 1, ORC_F_P = 2, ORC_F_A = 3 };
 enum { ORC_F32 = 0, ORC_BF16 = 1, ORC_F16 = 2 };
 enum { ORC_PH_DESCENT = 0, ORC_PH_REPAIR = 1, ORC_PH_LS = 2, ORC_PH_WAIT = 3 };
 enum {
@@ -71,7 +72,8 @@ typedef struct {
   int32_t repair;
   uint64_t seed;
   int32_t pool_k;     /* 0: independent trajectories (Alg. 1/2); K >= 1: pmQO pool (Alg. 3/4) */
-  int32_t pad0;
+  int32_t objective;  /* MaxCut relaxation: ORC_F_B (Eq. adj_lin_two_props), ORC_F_L (Eq. Cut QUBO),
+                         ORC_F_P (Eq. perturbed Laplacian cut), ORC_F_A (Eq. adj cut formulation) */
 } orc_params;
 
 /* Per-trajectory machine state, mirrored field by field for the tests. */
@@ -335,26 +337,69 @@ ORC_API void orc_eval_mis(const orc_graph* g, const uint8_t* z, int64_t out[4]) 
  * point is a PGA fixed point of f_B (Thm 3.6) iff for every v:
  * s_v = +1 and (As)_v <= -1, or s_v = -1 and (As)_v >= 0 (grad f_B =
  * -lambda 1 - 2 A s, 0 < lambda < 2, integer weights). */
-ORC_API void orc_eval_cut(const orc_graph* g, const uint8_t* z, int64_t out[4]) {
+/* The same with the fixed-point rule of another MaxCut relaxation, from
+ * the sign of its gradient at the binary point s (d_v = sum of w_vu):
+ *   f_L = 1/4 s'Ls:        grad = 1/2 (d_v s_v - (As)_v)
+ *   f_P = s'(L + lambda I)s: grad = 2 (d_v s_v - (As)_v + lambda s_v)
+ *   f_A = -s'As:           grad = -2 (As)_v
+ * s_v = +1 is fixed iff grad_v >= 0 and s_v = -1 iff grad_v <= 0. */
+ORC_API void orc_eval_cut_obj(const orc_graph* g, const uint8_t* z, int32_t objective, float lambda_,
+                              int64_t out[4]) {
   int64_t cut2 = 0, nonfixed = 0, cand = 0;
   for (int64_t v = 0; v < g->n; ++v) {
-    int64_t as = 0;
+    int64_t as = 0, d = 0;
     int sv = z[v] ? 1 : -1;
     for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) {
       int32_t u = g->col[j];
       int su = z[u] ? 1 : -1;
       as += (int64_t)wt(g, j) * su;
+      d += wt(g, j);
       if (z[u] != z[v]) cut2 += wt(g, j);
     }
     int64_t gain = sv * as;
     if (gain > 0) cand += 1;
-    int fixed = (sv == 1) ? (as <= -1) : (as >= 0);
+    int fixed;
+    switch (objective) {
+      case ORC_F_L: fixed = (sv == 1) ? (as <= d) : (as >= -d); break;
+      case ORC_F_P: fixed = (sv == 1) ? ((double)(as - d) <= (double)lambda_)
+                                      : ((double)(-(as + d)) <= (double)lambda_); break;
+      case ORC_F_A: fixed = (sv == 1) ? (as <= 0) : (as >= 0); break;
+      default: fixed = (sv == 1) ? (as <= -1) : (as >= 0); break;
+    }
     if (!fixed) nonfixed += 1;
   }
   out[0] = cut2 / 2;
   out[1] = nonfixed;
   out[2] = cand;
   out[3] = 0;
+}
+
+ORC_API void orc_eval_cut(const orc_graph* g, const uint8_t* z, int64_t out[4]) {
+  orc_eval_cut_obj(g, z, ORC_F_B, 0.001f, out);
+}
+
+/* The ascent direction of a step at x_v given acc = (Ax)_v (float, CSR
+ * order): MIS grad h = 1 - gamma (Ax)_v; MaxCut, by relaxation:
+ *   f_B: -lambda - 2 (Ax)_v;   f_A: -2 (Ax)_v;
+ *   f_L: 1/2 (d_v x_v - (Ax)_v);   f_P: 2 ((d_v x_v - (Ax)_v) + lambda x_v),
+ * d_v the (weighted) degree; every operation rounds once, as written. */
+static float step_grad(const orc_graph* g, const orc_params* p, int64_t v, float xv, float acc) {
+  if (p->problem == ORC_MIS) {
+    float t = p->gamma * acc;
+    return 1.0f - t;
+  }
+  if (p->objective == ORC_F_B || p->objective == ORC_F_A) {
+    float t = 2.0f * acc;
+    return p->objective == ORC_F_B ? -p->lambda_ - t : -t;
+  }
+  int64_t d = 0;
+  for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) d += wt(g, j);
+  float t1 = (float)d * xv;
+  float t2 = t1 - acc;
+  if (p->objective == ORC_F_L) return 0.5f * t2;
+  float t3 = p->lambda_ * xv;
+  float t4 = t2 + t3;
+  return 2.0f * t4;
 }
 
 /* threshold rounding (Sec. 3): MIS I = {x_v > 0.5}; MaxCut S = {x_v > 0} */
@@ -380,7 +425,7 @@ ORC_API void orc_descent_step(const orc_graph* g, const orc_params* p, const flo
     orc_eval_mis(g, z_out, tmp);
     ev[0] = tmp[0]; ev[1] = tmp[2]; ev[2] = tmp[3]; ev[3] = 0;
   } else {
-    orc_eval_cut(g, z_out, tmp);
+    orc_eval_cut_obj(g, z_out, p->objective, p->lambda_, tmp);
     ev[0] = tmp[0]; ev[1] = tmp[1]; ev[2] = tmp[2]; ev[3] = 0;
   }
   for (int64_t v = 0; v < g->n; ++v) {
@@ -390,14 +435,7 @@ ORC_API void orc_descent_step(const orc_graph* g, const orc_params* p, const flo
       if (wt(g, j) >= 0) acc = acc + xu;
       else acc = acc - xu;
     }
-    float grad;
-    if (p->problem == ORC_MIS) {
-      float t = p->gamma * acc;
-      grad = 1.0f - t;
-    } else {
-      float t = 2.0f * acc;
-      grad = -p->lambda_ - t;
-    }
+    float grad = step_grad(g, p, v, x[v], acc);
     float a = p->momentum * V[v];
     float b = p->alpha * grad;
     float vn = a + b;
@@ -421,14 +459,7 @@ ORC_API void orc_step_rows(const orc_graph* g, const orc_params* p, const float*
       if (wt(g, j) >= 0) acc = acc + xu;
       else acc = acc - xu;
     }
-    float grad;
-    if (p->problem == ORC_MIS) {
-      float t = p->gamma * acc;
-      grad = 1.0f - t;
-    } else {
-      float t = 2.0f * acc;
-      grad = -p->lambda_ - t;
-    }
+    float grad = step_grad(g, p, v, x[v], acc);
     float a = p->momentum * V[v];
     float b = p->alpha * grad;
     float vn = a + b;
@@ -1112,6 +1143,50 @@ ORC_API double orc_objective_f64(const orc_graph* g, int32_t problem, double gam
   }
   if (problem == ORC_MIS) return lin - 0.5 * gamma * quad;
   return -lambda_ * lin - quad;
+}
+
+/* The four MaxCut relaxations of Sec. 3 in double precision, written from
+ * their definitions: f_L = 1/4 x'Lx (on {-1,1}^n equal to 1/2 sum over
+ * undirected edges of w(1 - x_u x_v), the cut), f_P = x'(L + lambda I)x,
+ * f_A = -x'Ax, f_B = -lambda 1'x - x'Ax, with L = D - A; and their
+ * gradients (derived: 1/2 Lx, 2(L + lambda I)x, -2Ax, -lambda 1 - 2Ax). */
+ORC_API double orc_cut_objective_f64(const orc_graph* g, int32_t objective, double lambda_, const double* x) {
+  double xax = 0.0, xdx = 0.0, xx = 0.0, lin = 0.0;
+  for (int64_t v = 0; v < g->n; ++v) {
+    double d = 0.0, ax = 0.0;
+    for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) {
+      const double w = (double)wt(g, j);
+      d += w;
+      ax += w * x[g->col[j]];
+    }
+    xax += x[v] * ax;
+    xdx += d * x[v] * x[v];
+    xx += x[v] * x[v];
+    lin += x[v];
+  }
+  switch (objective) {
+    case ORC_F_L: return 0.25 * (xdx - xax);
+    case ORC_F_P: return (xdx - xax) + lambda_ * xx;
+    case ORC_F_A: return -xax;
+    default: return -lambda_ * lin - xax;
+  }
+}
+
+ORC_API void orc_cut_gradient_f64(const orc_graph* g, int32_t objective, double lambda_, const double* x,
+                                  double* grad) {
+  for (int64_t v = 0; v < g->n; ++v) {
+    double d = 0.0, ax = 0.0;
+    for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) {
+      d += (double)wt(g, j);
+      ax += (double)wt(g, j) * x[g->col[j]];
+    }
+    switch (objective) {
+      case ORC_F_L: grad[v] = 0.5 * (d * x[v] - ax); break;
+      case ORC_F_P: grad[v] = 2.0 * (d * x[v] - ax + lambda_ * x[v]); break;
+      case ORC_F_A: grad[v] = -2.0 * ax; break;
+      default: grad[v] = -lambda_ - 2.0 * ax; break;
+    }
+  }
 }
 
 ORC_API void orc_gradient_f64(const orc_graph* g, int32_t problem, double gamma, double lambda_, const double* x,
