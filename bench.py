@@ -37,6 +37,7 @@ import numpy as np  # noqa: E402
 import mqo_inputs as mi  # noqa: E402
 
 METRIC = "edge-updates/s of fused mQO steps"
+OBJECTIVES = {"fb": 0, "fl": 1, "fp": 2, "fa": 3}
 UNIT = "edge-updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -73,20 +74,48 @@ def _oracle_job(args):
     G = mi.Graph(n, rp, col, w)
     og = oracle.Graph(G)
     p = oracle.params(**pdict)
+    if pdict.get("pool_k", 0) > 0:
+        # pool mode: the B trajectories of one member graph run together
+        B = pdict["batch"]
+        pg = oracle.PoolGraph(og, p, traj, B)
+        t0 = time.perf_counter()
+        pg.run(ticks)
+        return time.perf_counter() - t0, int(rp[-1]) * ticks * B, pg.pool.best
     tr = oracle.Trajectory(og, p, traj)
     t0 = time.perf_counter()
     tr.run(ticks)
     return time.perf_counter() - t0, int(rp[-1]) * ticks, tr.state["best"]
 
 
-def oracle_sample(G, wl, x_dtype, v_dtype, target_s=12.0, cores=None):
-    """Time the oracle on a bounded sample of the workload's trajectories."""
+def oracle_sample(G, wl, x_dtype, v_dtype, target_s=12.0, cores=None, pool_k=0, objective=0):
+    """Time the oracle on a bounded sample of the workload's trajectories
+    (pool mode: of its member graphs, each with its B trajectories)."""
     cores = cores or os.cpu_count() or 1
     pd = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
                              "sigma") if k in wl}
     pd.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), x_dtype=x_dtype, v_dtype=v_dtype,
-              seed=0)
+              seed=0, pool_k=pool_k, objective=objective)
     B = wl["batch"]
+    if pool_k > 0:
+        sub = G.subgraph(0)
+        dt, eu, _ = _oracle_job((0, sub.row_ptr, sub.col_idx, sub.weights, sub.n, pd, 0, 10))
+        rate1 = eu / max(dt, 1e-9)
+        ticks = 100
+        ngr = max(cores, int(target_s * rate1 * cores / (sub.nnz * B * ticks)))
+        ngr = min(ngr, G.num_graphs)
+        jobs = []
+        for g in range(ngr):
+            sg = G.subgraph(g)
+            jobs.append((g, sg.row_ptr, sg.col_idx, sg.weights, sg.n, pd, g * B, ticks))
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        eu = sum(r[1] for r in res)
+        return dict(value=eu / wall, unit=UNIT, cores=cores, kind="oracle",
+                    sample=f"{ngr} member graphs x {B} trajectories (pool mode, K={pool_k}) x {ticks} ticks of the "
+                           f"same workload, {eu:.3e} edge-updates in {wall:.2f} s wall on {cores} processes")
     # probe one trajectory to size the sample
     sub = G.subgraph(0)
     job = (0, sub.row_ptr, sub.col_idx, sub.weights, sub.n, pd, 0, 20)
@@ -124,9 +153,10 @@ def reference_arm(args):
     per_step = []
     base = None
     for _ in range(args.warmup):
-        oracle_sample(G, wl, xd, vd, target_s=0.5)
+        oracle_sample(G, wl, xd, vd, target_s=0.5, pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
     for _ in range(args.steps):
-        base = oracle_sample(G, wl, xd, vd, target_s=max(1.0, 60.0 / max(args.steps, 1)))
+        base = oracle_sample(G, wl, xd, vd, target_s=max(1.0, 60.0 / max(args.steps, 1)), pool_k=args.pool_k,
+                             objective=OBJECTIVES[args.objective])
         per_step.append(base["value"])
     value = statistics.median(per_step)
     nnz_b = G.nnz * wl["batch"]
@@ -135,7 +165,7 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": nnz_b / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "x_dtype": args.x_dtype, "v_dtype": args.v_dtype or args.x_dtype,
-                   "nnz": G.nnz, "batch": wl["batch"]},
+                   "nnz": G.nnz, "batch": wl["batch"], "pool_k": args.pool_k, "objective": args.objective},
         "cpu_baseline": dict(base, value=value),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -270,7 +300,8 @@ def gpu_arm(args):
     B = wl["batch"]
     pkw = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
                               "sigma")}
-    pkw.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), seed=1000 * rank)
+    pkw.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), seed=1000 * rank,
+               pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -278,6 +309,8 @@ def gpu_arm(args):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    info_launches = [0]
 
     def measure(x_dtype, v_dtype, steps, warmup, sample_clocks, autotune=False):
         g = mq.Graph(G)
@@ -294,6 +327,7 @@ def gpu_arm(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         phase_ms, launches = s.run_timed(steps)
+        info_launches[0] = launches
         e1.record()
         torch.cuda.synchronize()
         barrier()
@@ -311,6 +345,7 @@ def gpu_arm(args):
 
     nnz_b = G.nnz * B
     ms, phase_ms, clocks, best_vals, plan = measure(xd, vd, args.steps, args.warmup, True, not args.no_autotune)
+    timed_launches = info_launches[0]
     step_avg_ms = phase_ms["step"] / args.steps
     ms, value = aggregate_ranks(ms, float(nnz_b) * args.steps, dist, "cuda")
 
@@ -403,7 +438,7 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(G, wl, xd, vd, target_s=12.0)
+        cpu = oracle_sample(G, wl, xd, vd, target_s=12.0, pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
 
     if rank == 0:
         line = {
@@ -412,8 +447,9 @@ def gpu_arm(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "x_dtype": args.x_dtype, "v_dtype": args.v_dtype or args.x_dtype,
                        "nnz": G.nnz, "nodes": G.n, "batch": B, "edge_updates_per_step": nnz_b,
-                       "l2": "inputs larger than L2 (CSR + state > 126 MB)", "parallelism": f"replicas x{world}"},
-            "roofline": roof, "e2e": e2e, "gpu_launches": 7 * args.steps,
+                       "l2": "inputs larger than L2 (CSR + state > 126 MB)", "parallelism": f"replicas x{world}",
+                       "pool_k": args.pool_k, "objective": args.objective},
+            "roofline": roof, "e2e": e2e, "gpu_launches": timed_launches,
             "kernel_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
             "clocks": clocks, "best_mean": float(np.mean(best_vals)), "best_max": int(np.max(best_vals)),
         }
@@ -441,6 +477,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--pool-k", type=int, default=0, help="pmQO pool of K sets per graph (0: Alg. 1/2)")
+    ap.add_argument("--objective", default="fb", choices=sorted(OBJECTIVES), help="MaxCut relaxation")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

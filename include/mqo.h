@@ -60,10 +60,20 @@ typedef enum {
 } mqo_status;
 
 typedef enum { MQO_MIS = 0, MQO_MAXCUT = 1 } mqo_problem;
+/* MaxCut relaxation descended by the solver (Sec. 3):
+ *   MQO_OBJ_FB  f_B(x) = -lambda 1'x - x'Ax        (Eq. adj_lin_two_props; the default)
+ *   MQO_OBJ_FL  f_L(x) = 1/4 x'Lx, L = D - A       (Eq. Cut QUBO)
+ *   MQO_OBJ_FP  f_P(x) = x'(L + lambda I)x         (perturbed Laplacian)
+ *   MQO_OBJ_FA  f_A(x) = -x'Ax                     (adjacency form)
+ * Each equals an affine function of the cut on {-1,1}^n; they differ in
+ * which binary points are PGA fixed points (Thm 3.3, Prop. 3.4, Thm 3.6). */
+typedef enum { MQO_OBJ_FB = 0, MQO_OBJ_FL = 1, MQO_OBJ_FP = 2, MQO_OBJ_FA = 3 } mqo_objective;
 typedef enum { MQO_F32 = 0, MQO_BF16 = 1, MQO_F16 = 2 } mqo_dtype;
 
 /* Trajectory phases reported by mqo_traj_state. */
-typedef enum { MQO_PH_DESCENT = 0, MQO_PH_REPAIR = 1, MQO_PH_LS = 2 } mqo_phase;
+/* MQO_PH_WAIT (pool mode only): the trajectory holds a finished set until
+ * every trajectory of its member graph has one (Alg. 3/4 steps 3-4). */
+typedef enum { MQO_PH_DESCENT = 0, MQO_PH_REPAIR = 1, MQO_PH_LS = 2, MQO_PH_WAIT = 3 } mqo_phase;
 
 /*
  * Solver parameters.  Paper symbols: alpha (step size), momentum (MGA,
@@ -90,6 +100,9 @@ typedef struct {
   int32_t local_search; /* 1: OneTwoSwap / OneTwoFlip after t_gs rounds (Alg. 1/2 step 11) */
   int32_t repair;       /* MIS: 1 = repair a capped descent into a maximal IS, 0 = discard it */
   uint64_t seed;
+  int32_t objective;    /* MaxCut only: mqo_objective (gradient of the step and its fixed-point test) */
+  int32_t pool_k;       /* 0: B independent trajectories per graph (Alg. 1/2); K in [1,64]: the B
+                           trajectories of a graph share a pool of the K best sets (pmQO, Alg. 3/4) */
 } mqo_params;
 
 /* Per-trajectory machine state (host copy), see mqo_traj_state. */
@@ -108,6 +121,8 @@ typedef struct {
   int64_t ev_b;         /* MIS uncovered nodes | MaxCut nodes with a positive 1-flip gain */
   int64_t accepts;      /* strict improvements of best */
   int64_t descents;     /* finished descents */
+  int64_t held;         /* pool mode: value of the set held while waiting, INT64_MIN if none
+                           (or a capped, unrepaired MIS point, which is no candidate) */
 } mqo_traj_info;
 
 /* ---------------------------------------------------------------- graphs */
@@ -174,7 +189,8 @@ MQO_API mqo_status mqo_step(mqo_solver s, int32_t nsteps);
 /*
  * Exact evaluation of z(x_t) made by the last mqo_step, per trajectory,
  * into device int64 arrays of length G*B (any may be NULL): value (MIS
- * size | cut), a (MIS conflicting nodes | MaxCut non-fixed nodes),
+ * size | cut), a (MIS conflicting nodes | MaxCut nodes that a PGA step of
+ * the solver's relaxation would move, i.e. not fixed under it),
  * b (MIS uncovered nodes | MaxCut positive-gain nodes).
  */
 MQO_API mqo_status mqo_step_stats(mqo_solver s, int64_t* value, int64_t* a, int64_t* b);
@@ -183,7 +199,8 @@ MQO_API mqo_status mqo_step_stats(mqo_solver s, int64_t* value, int64_t* a, int6
  * nticks ticks of the full per-trajectory machine (Alg. 1 / Alg. 2 with a
  * tick budget in place of the wall clock): each tick every trajectory
  * takes one descent step or one discrete round; descents end at the
- * fixed-point test (Eq. MIS checking; f_B fixed point, Thm 3.6) or at
+ * fixed-point test (Eq. MIS checking; for MaxCut the fixed point of the
+ * solver's relaxation, e.g. f_B, Thm 3.6) or at
  * descent_cap; strict acceptance (Alg. 1 steps 4/10); reset rounds from the
  * best set (steps 6-8); local search after t_gs rounds (step 11); a fresh
  * initialisation after local search.  The tick loop runs as a captured
@@ -196,7 +213,8 @@ MQO_API mqo_status mqo_run(mqo_solver s, int64_t nticks);
  * whose byte in traj_mask (device, G*B bytes; NULL = all) is non-zero:
  * x <- best set (MIS 1/0, MaxCut +1/-1), x_R <- 0 with |R| = floor(rho n_g)
  * drawn from the trajectory's reset stream for round r+1, V <- 0, and the
- * trajectory starts a new descent.
+ * trajectory starts a new descent.  MQO_EINVAL in pool mode, where resets
+ * start from pool members chosen by the pool machine.
  */
 MQO_API mqo_status mqo_reset(mqo_solver s, const uint8_t* traj_mask);
 
@@ -220,7 +238,8 @@ MQO_API mqo_status mqo_evaluate(mqo_solver s, const uint32_t* z_bits, int64_t* v
  * (OneTwoSwap for MIS, OneTwoFlip for MaxCut; Sec. 4 and Defs. 2.3-2.5):
  * rounds are applied until none changes the set, then the result is
  * accepted if it is strictly better.  Synchronises the stream (the number
- * of rounds is data dependent; max_rounds bounds it).
+ * of rounds is data dependent; max_rounds bounds it).  MQO_EINVAL in pool
+ * mode, where the pool machine runs its own local search (Alg. 3/4 step 13).
  */
 MQO_API mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds);
 
@@ -244,6 +263,18 @@ MQO_API mqo_status mqo_solve(mqo_solver s, int64_t nticks);
  * Synchronises the stream.
  */
 MQO_API mqo_status mqo_best(mqo_solver s, int64_t* values, uint32_t* z_bits);
+
+/*
+ * Pool readout (pool mode, pool_k = K > 0; pmQO, Alg. 3/4): for every member
+ * graph g, counts[g] (host int32[G]) = pool members so far (<= K), values
+ * (host int64[G*K]) = their exact values, best first (entries beyond
+ * counts[g] undefined), merges (host int64[G]) = pool merges so far, and
+ * bits (device, n*Kw uint32 words, Kw = ceil(K/32)) = the member sets,
+ * node-major: member k of node v is bit k%32 of word v*Kw + k/32.  Any
+ * pointer may be NULL.  MQO_EINVAL if the solver is not in pool mode.
+ * Synchronises the stream.
+ */
+MQO_API mqo_status mqo_pool_state(mqo_solver s, int32_t* counts, int64_t* values, int64_t* merges, uint32_t* bits);
 
 /* Per-trajectory machine state (host array of G*B mqo_traj_info).  Synchronises. */
 MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
@@ -290,7 +321,8 @@ MQO_API mqo_status mqo_get_v(mqo_solver s, void* v_out);
 
 /*
  * Relaxed objective of the current x per trajectory, in double precision
- * (h of Eq. MIS QUBO or f_B of Eq. adj_lin_two_props), into device double
+ * (h of Eq. MIS QUBO, or the solver's MaxCut relaxation: f_B of
+ * Eq. adj_lin_two_props, f_L, f_P or f_A of Sec. 3), into device double
  * out[G*B].  (Ax)_v is accumulated in float32 in CSR order; products and
  * sums are in double.
  */

@@ -17,11 +17,12 @@ from . import build as _build
 __all__ = [
     "MqoError", "Params", "TrajInfo", "Graph", "Solver", "params", "lib", "fb_forward", "spmm_grad",
     "pga_momentum_step", "pga_adam_step", "FbObjective", "PGAMomentum", "PGAAdam",
-    "MIS", "MAXCUT", "F32", "BF16", "F16",
+    "MIS", "MAXCUT", "F32", "BF16", "F16", "OBJ_FB", "OBJ_FL", "OBJ_FP", "OBJ_FA",
 ]
 
 MIS, MAXCUT = 0, 1
 F32, BF16, F16 = 0, 1, 2
+OBJ_FB, OBJ_FL, OBJ_FP, OBJ_FA = 0, 1, 2, 3
 INT64_MIN = -(1 << 63)
 _STATUS = {0: "MQO_OK", -1: "MQO_EINVAL", -2: "MQO_EGRAPH", -3: "MQO_ENOMEM", -4: "MQO_ECUDA",
            -5: "MQO_ETIMEOUT", -6: "MQO_ESTATE"}
@@ -39,6 +40,7 @@ class Params(C.Structure):
         ("alpha", C.c_float), ("momentum", C.c_float), ("gamma", C.c_float), ("lambda_", C.c_float),
         ("rho", C.c_double), ("sigma", C.c_float), ("t_gs", C.c_int32), ("descent_cap", C.c_int32),
         ("init_kind", C.c_int32), ("local_search", C.c_int32), ("repair", C.c_int32), ("seed", C.c_uint64),
+        ("objective", C.c_int32), ("pool_k", C.c_int32),
     ]
 
 
@@ -47,7 +49,7 @@ class TrajInfo(C.Structure):
         ("phase", C.c_int32), ("s", C.c_int32), ("r", C.c_int32), ("o", C.c_int32),
         ("best", C.c_int64), ("ticks", C.c_int64), ("last_round", C.c_int32), ("pad0", C.c_int32),
         ("last_commits", C.c_int64), ("ev_value", C.c_int64), ("ev_a", C.c_int64), ("ev_b", C.c_int64),
-        ("accepts", C.c_int64), ("descents", C.c_int64),
+        ("accepts", C.c_int64), ("descents", C.c_int64), ("held", C.c_int64),
     ]
 
     def as_dict(self):
@@ -55,11 +57,12 @@ class TrajInfo(C.Structure):
 
 
 def params(problem=MIS, batch=1, x_dtype=F32, v_dtype=None, alpha=0.8, momentum=0.3, gamma=2.0, lambda_=0.001,
-           rho=0.7, sigma=0.1, t_gs=60, descent_cap=50, init_kind=0, local_search=1, repair=1, seed=0) -> Params:
+           rho=0.7, sigma=0.1, t_gs=60, descent_cap=50, init_kind=0, local_search=1, repair=1, seed=0,
+           objective=0, pool_k=0) -> Params:
     if v_dtype is None:
         v_dtype = x_dtype
     return Params(problem, batch, x_dtype, v_dtype, alpha, momentum, gamma, lambda_, rho, sigma, t_gs,
-                  descent_cap, init_kind, local_search, repair, seed)
+                  descent_cap, init_kind, local_search, repair, seed, objective, pool_k)
 
 
 _lib = None
@@ -85,6 +88,7 @@ _SIGS = {
     "mqo_run_timed": [_P, C.c_int64, _P, _P],
     "mqo_best": [_P, _P, _P],
     "mqo_traj_state": [_P, _P],
+    "mqo_pool_state": [_P, _P, _P, _P, _P],
     "mqo_solver_info": [_P, _P, _P, _P, _P],
     "mqo_autotune": [_P, C.c_int32, _P, _P],
     "mqo_get_x": [_P, _P],
@@ -284,6 +288,18 @@ class Solver:
         return {"step_kernel": ("smem_wide" if p & 4 else "smem") if p & 1 else "global",
                 "discrete_kernel": "graph" if p & 2 else "pairs",
                 "lanes_vec": p >> 4, "ms_per_tick": ms.value}
+
+    def pool_state(self):
+        """Pool mode: (counts [G], values [G, K], merges [G]) on the host and the
+        members' bits (device words, n * ceil(K/32))."""
+        K = self.p.pool_k
+        G = self.graph.num_graphs
+        counts = np.zeros(G, dtype=np.int32)
+        values = np.zeros(G * K, dtype=np.int64)
+        merges = np.zeros(G, dtype=np.int64)
+        bits = self._torch.zeros(self.graph.n * ((K + 31) // 32), dtype=self._torch.int32, device="cuda")
+        _check(lib().mqo_pool_state(self.handle, _hptr(counts), _hptr(values), _hptr(merges), _dptr(bits)))
+        return counts, values.reshape(G, K), merges, bits
 
     def traj_state(self):
         arr = (TrajInfo * self.T)()

@@ -378,6 +378,10 @@ cudaError_t enqueue_tick(mqo_solver s) {
   cudaError_t e;
   const SolverDev& S = s->S;
   const int G = S.g.num_graphs;
+  if (S.K > 0) {  // pmQO: the graphs' pool decisions come first
+    if ((e = launch_pool_ctrl(S, s->work)) != cudaSuccess) return e;
+    if ((e = launch_pool_apply(S, s->work)) != cudaSuccess) return e;
+  }
   if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
   if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
   if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work)) != cudaSuccess) return e;
@@ -506,6 +510,9 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
   if (p->t_gs < 0) return fail(MQO_EINVAL, "t_gs must be >= 0");
   if (!(p->rho >= 0.0 && p->rho < 1.0)) return fail(MQO_EINVAL, "rho must lie in [0,1)");
   if (p->init_kind != 0 && p->init_kind != 1) return fail(MQO_EINVAL, "init_kind must be 0 or 1");
+  if (p->objective < MQO_OBJ_FB || p->objective > MQO_OBJ_FA) return fail(MQO_EINVAL, "unknown objective %d", p->objective);
+  if (p->problem == MQO_MIS && p->objective != MQO_OBJ_FB) return fail(MQO_EINVAL, "objective applies to MaxCut only");
+  if (p->pool_k < 0 || p->pool_k > kPoolMax) return fail(MQO_EINVAL, "pool_k=%d must lie in [0,%d]", p->pool_k, kPoolMax);
 
   auto* s = new mqo_solver_s();
   s->g = g;
@@ -537,6 +544,8 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
   S.p.local_search = p->local_search;
   S.p.repair = p->repair;
   S.p.seed = p->seed;
+  S.p.objective = p->objective;
+  S.p.pool_k = p->pool_k;
   S.B = B;
   S.Bw = (B + 31) / 32;
   const int64_t n = g->n, T = (int64_t)g->G * B;
@@ -586,6 +595,15 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     s->disc_smem = pairs ? 0 : s->disc_smem_max;
   }
   const size_t TR = (size_t)T * S.R;
+  S.K = p->pool_k;
+  S.Kw = (p->pool_k + 31) / 32;
+  if (S.K > 0) {
+    if ((st = dalloc(&S.Pool, (size_t)n * S.Kw, &s->allocs)) != MQO_OK) return bail(st);
+    if ((st = dalloc(&S.pool, (size_t)g->G, &s->allocs)) != MQO_OK) return bail(st);
+    if ((st = dalloc(&S.psrc, (size_t)g->G * S.K, &s->allocs)) != MQO_OK) return bail(st);
+    if ((st = dalloc(&S.pval, (size_t)g->G * S.K, &s->allocs)) != MQO_OK) return bail(st);
+    if ((st = dalloc(&S.pbase, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
+  }
   if ((st = dalloc(&S.st, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.act, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&S.rnd, (size_t)T, &s->allocs)) != MQO_OK) return bail(st);
@@ -641,6 +659,12 @@ mqo_status mqo_init(mqo_solver s) {
   CKS(cudaMemsetAsync(S.pb, 0xff, s->pairs * sizeof(int32_t), s->work));
   CKS(cudaMemsetAsync(S.gain, 0, s->pairs * sizeof(int32_t), s->work));
   CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B * S.R, s->work));
+  if (S.K > 0) {
+    CKS(cudaMemsetAsync(S.Pool, 0, (size_t)S.g.n * S.Kw * sizeof(uint32_t), s->work));
+    CKS(cudaMemsetAsync(S.pval, 0, (size_t)S.g.num_graphs * S.K * sizeof(int64_t), s->work));
+    CKS(cudaMemsetAsync(S.psrc, 0, (size_t)S.g.num_graphs * S.K * sizeof(int32_t), s->work));
+    CKS(cudaMemsetAsync(S.pbase, 0xff, (size_t)S.g.num_graphs * S.B * sizeof(int32_t), s->work));
+  }
   CKS(launch_state_init(S, s->work));
   CKS(launch_apply(S, s->work));
   return MQO_OK;
@@ -685,6 +709,8 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t
       cudaEvent_t* e = &ev[(size_t)(kPhases + 1) * k];
       int i = 0;
       ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
+      if (ek == cudaSuccess && S.K > 0) ek = launch_pool_ctrl(S, s->work);  // pool kernels count as control
+      if (ek == cudaSuccess && S.K > 0) ek = launch_pool_apply(S, s->work);
       if (ek == cudaSuccess) ek = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work);
       if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       if (ek == cudaSuccess) ek = launch_apply(S, s->work);
@@ -724,7 +750,9 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t
   s->host_tick += nticks;
   if (phase_ms)
     for (int p = 0; p < kPhases; ++p) phase_ms[p] = tot[p];
-  if (launches) *launches = (int64_t)kPhases * nticks;
+  // five kernels per tick with the fused discrete kernel, seven with the
+  // three node-parallel passes
+  if (launches) *launches = (int64_t)((s->disc_smem > 0 ? 5 : 7) + (s->S.K > 0 ? 2 : 0)) * nticks;
   return MQO_OK;
 }
 
@@ -757,6 +785,7 @@ mqo_status mqo_step_stats(mqo_solver s, int64_t* value, int64_t* a, int64_t* b) 
 
 mqo_status mqo_reset(mqo_solver s, const uint8_t* traj_mask) {
   CHECK_SOLVER(s);
+  if (s->S.K > 0) return fail(MQO_EINVAL, "mqo_reset is not available in pool mode (the pool machine resets)");
   Scope sc(s);
   CKS(launch_ctrl(s->S, CTRL_RESET, traj_mask, s->work));
   CKS(launch_apply(s->S, s->work));
@@ -786,6 +815,7 @@ mqo_status mqo_evaluate(mqo_solver s, const uint32_t* z_bits, int64_t* value, in
 mqo_status mqo_local_search(mqo_solver s, int32_t max_rounds) {
   CHECK_SOLVER(s);
   if (max_rounds < 1) return fail(MQO_EINVAL, "max_rounds must be >= 1");
+  if (s->S.K > 0) return fail(MQO_EINVAL, "mqo_local_search is not available in pool mode (the pool machine searches)");
   Scope sc(s);
   SolverDev& S = s->S;
   const size_t T = (size_t)S.g.num_graphs * S.B;
@@ -862,6 +892,29 @@ mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_byt
   return MQO_OK;
 }
 
+mqo_status mqo_pool_state(mqo_solver s, int32_t* counts, int64_t* values, int64_t* merges, uint32_t* bits) {
+  CHECK_SOLVER(s);
+  const SolverDev& S = s->S;
+  if (S.K == 0) return fail(MQO_EINVAL, "the solver is not in pool mode (pool_k = 0)");
+  const int G = S.g.num_graphs;
+  std::vector<PoolState> ps((size_t)G);
+  {
+    Scope sc(s);
+    if (bits)
+      CKS(cudaMemcpyAsync(bits, S.Pool, (size_t)S.g.n * S.Kw * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s->work));
+    CKS(cudaMemcpyAsync(ps.data(), S.pool, (size_t)G * sizeof(PoolState), cudaMemcpyDeviceToHost, s->work));
+    if (values)
+      CKS(cudaMemcpyAsync(values, S.pval, (size_t)G * S.K * sizeof(int64_t), cudaMemcpyDeviceToHost, s->work));
+  }
+  CKS(cudaStreamSynchronize(s->work));
+  CKS(cudaStreamSynchronize(s->user));
+  for (int g = 0; g < G; ++g) {
+    if (counts) counts[g] = ps[(size_t)g].count;
+    if (merges) merges[g] = ps[(size_t)g].merges;
+  }
+  return MQO_OK;
+}
+
 mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
   CHECK_SOLVER(s);
   if (!out) return fail(MQO_EINVAL, "null out");
@@ -884,11 +937,15 @@ mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
       sum.b += c[i * R + r].b;
       sum.commits += c[i * R + r].commits;
     }
-    const int64_t cv = (int64_t)sum.value;
-    h[i].ev_value = mis ? cv : cv / 2;
-    h[i].ev_a = (int64_t)sum.a;
-    h[i].ev_b = (int64_t)sum.b;
-    h[i].last_commits = (int64_t)sum.commits;
+    // (in pool mode only if the trajectory worked in that tick: a waiting
+    // trajectory keeps its last evaluation)
+    if (s->S.K == 0 || (h[i].act & ACT_STEP) || h[i].round != RD_NONE) {
+      const int64_t cv = (int64_t)sum.value;
+      h[i].ev_value = mis ? cv : cv / 2;
+      h[i].ev_a = (int64_t)sum.a;
+      h[i].ev_b = (int64_t)sum.b;
+      h[i].last_commits = (int64_t)sum.commits;
+    }
     mqo_traj_info& o = out[i];
     const TrajState& t = h[i];
     o.phase = t.phase;
@@ -905,6 +962,7 @@ mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
     o.ev_b = t.ev_b;
     o.accepts = t.accepts;
     o.descents = t.descents;
+    o.held = t.held;
   }
   return MQO_OK;
 }
@@ -1018,7 +1076,10 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
       {S.Zaux, s->words * 4}, {S.Zfree, s->words * 4}, {S.Zdrop, s->words * 4},
       {S.owner, s->pairs * 4}, {S.pa, s->pairs * 4}, {S.pb, s->pairs * 4}, {S.gain, s->pairs * 4},
       {S.st, T * sizeof(TrajState)}, {S.act, T * 4}, {S.rnd, T * 4}, {S.bestv, T * 8},
-      {S.cnt, T * S.R * sizeof(Counters)}, {S.tick, 8}, {S.gflag, (size_t)3 * S.g.num_graphs * 4}, {S.any, 16}};
+      {S.cnt, T * S.R * sizeof(Counters)}, {S.tick, 8}, {S.gflag, (size_t)3 * S.g.num_graphs * 4}, {S.any, 16},
+      {S.Pool, (size_t)S.g.n * S.Kw * 4}, {S.pool, (size_t)(S.K > 0 ? S.g.num_graphs : 0) * sizeof(PoolState)},
+      {S.psrc, (size_t)S.g.num_graphs * S.K * 4}, {S.pval, (size_t)S.g.num_graphs * S.K * 8},
+      {S.pbase, (size_t)(S.K > 0 ? T : 0) * 4}};
   size_t total = 0;
   for (const Buf& b : bufs) total += (b.n + 255) & ~(size_t)255;
   char* snap = nullptr;
@@ -1055,14 +1116,14 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     Scope sc(s);
     size_t off = 0;
     for (const Buf& b : bufs) {
-      if (err == cudaSuccess) err = cudaMemcpyAsync(snap + off, b.p, b.n, cudaMemcpyDeviceToDevice, s->work);
+      if (err == cudaSuccess && b.n > 0) err = cudaMemcpyAsync(snap + off, b.p, b.n, cudaMemcpyDeviceToDevice, s->work);
       off += (b.n + 255) & ~(size_t)255;
     }
     for (const Plan& pl : plans) {
       if (err != cudaSuccess) break;
       off = 0;
       for (const Buf& b : bufs) {
-        if (err == cudaSuccess) err = cudaMemcpyAsync(b.p, snap + off, b.n, cudaMemcpyDeviceToDevice, s->work);
+        if (err == cudaSuccess && b.n > 0) err = cudaMemcpyAsync(b.p, snap + off, b.n, cudaMemcpyDeviceToDevice, s->work);
         off += (b.n + 255) & ~(size_t)255;
       }
       s->step_smem = pl.step_smem;
@@ -1083,7 +1144,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     }
     off = 0;
     for (const Buf& b : bufs) {
-      if (err == cudaSuccess) err = cudaMemcpyAsync(b.p, snap + off, b.n, cudaMemcpyDeviceToDevice, s->work);
+      if (err == cudaSuccess && b.n > 0) err = cudaMemcpyAsync(b.p, snap + off, b.n, cudaMemcpyDeviceToDevice, s->work);
       off += (b.n + 255) & ~(size_t)255;
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(s->work);

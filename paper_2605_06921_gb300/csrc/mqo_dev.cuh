@@ -14,7 +14,16 @@ namespace mqo {
 
 enum : int { PROB_MIS = 0, PROB_MAXCUT = 1 };
 enum : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
-enum : int { PH_DESCENT = 0, PH_REPAIR = 1, PH_LS = 2, PH_IDLE = 3 };
+// MaxCut relaxations of Sec. 3: f_B (Eq. adj_lin_two_props, the default),
+// f_L (Eq. Cut QUBO), f_P (perturbed Laplacian), f_A (adjacency form)
+enum : int { OBJ_FB = 0, OBJ_FL = 1, OBJ_FP = 2, OBJ_FA = 3 };
+// PH_WAIT (pool mode): the trajectory holds a finished set until every
+// trajectory of its graph has one (the batch of Alg. 3/4 steps 3-4)
+enum : int { PH_DESCENT = 0, PH_REPAIR = 1, PH_LS = 2, PH_WAIT = 3 };
+// graph-wide decisions of the pool machine for one tick
+enum : int { DEC_NONE = 0, DEC_NEXT = 1, DEC_LS = 2, DEC_OUTER = 3 };
+enum : int { EP_DESCENT = 0, EP_LS = 1 };
+constexpr int kPoolMax = 128;  // largest pool size K
 enum : int {
   RD_NONE = -1,
   RD_COUNT = 0,
@@ -33,6 +42,7 @@ enum : int {
   ACT_INIT = 16,       // x <- fresh initialisation, V <- 0 (Alg. 1 step 2)
   ACT_WORK_ZX = 32,    // work set <- z of the last step (repair entry)
   ACT_WORK_BEST = 64,  // work set <- best set (local-search entry)
+  ACT_POOL = 128,      // pool mode: RESET / WORK_BEST take pool slot pbase[t] (empty set if < 0) as base
   ACT_APPLY_MASK = ACT_ACC_ZX | ACT_ACC_WORK | ACT_RESET | ACT_INIT | ACT_WORK_ZX | ACT_WORK_BEST
 };
 
@@ -43,6 +53,8 @@ struct Params {
   float sigma;
   int32_t t_gs, cap, init_kind, local_search, repair;
   uint64_t seed;
+  int32_t objective;  // MaxCut relaxation (OBJ_*)
+  int32_t pool_k;     // 0: independent trajectories; K >= 1: pmQO pool of K sets per graph
 };
 
 // One trajectory of the tick machine (field meanings as mqo_traj_info).
@@ -56,6 +68,19 @@ struct __align__(16) TrajState {
   int32_t act, ls_done;
   uint32_t rkeys[6];
   int64_t rk;
+  int64_t held;  // pool mode: value of the held set (INT64_MIN: none, or not a candidate)
+};
+
+// Per member graph state of the pool machine (pmQO, Alg. 3/4).
+struct PoolState {
+  int32_t epoch;    // EP_DESCENT: trajectories finish descents; EP_LS: local searches
+  int32_t count;    // pool members (<= K)
+  int64_t best;     // value of the graph's best set (INT64_MIN before the first)
+  int64_t merges;   // pool merges so far
+  int32_t dec;      // decision of the current tick (DEC_*)
+  int32_t best_src; // best set replaced this tick from: 0 the new pool slot 0, K + b trajectory b's work set, -1 no
+  int32_t merged;   // 1 if the pool was rewritten this tick (psrc holds the sources of slots 0..count-1)
+  int32_t stamp;    // tick + 1 when pool bits or the best set must be rewritten this tick
 };
 
 // Per-trajectory integer sums produced by one tick (value of MaxCut is 2*cut).
@@ -112,6 +137,13 @@ struct SolverDev {
   int32_t* gflag;   // [3*G] tick stamps: any apply / any discrete / any step
   int32_t* any;     // [4] per-tick "any trajectory" stamps (apply, disc, step)
   int64_t* bestv;   // [G*B] best value of each trajectory (compact copy for readout)
+  // pool mode (p.pool_k = K > 0)
+  int32_t K, Kw;    // pool size, pool bit words per node
+  uint32_t* Pool;   // [n*Kw] pool sets, node-major: slot k of node v = bit k%32 of word v*Kw + k/32
+  PoolState* pool;  // [G]
+  int32_t* psrc;    // [G*K] source of new slot s of a merge: j < K old slot j, K + b trajectory b's work set
+  int64_t* pval;    // [G*K] values of the pool members, best first
+  int32_t* pbase;   // [G*B] pool slot a trajectory resets / searches from (-1: the empty set)
 };
 
 // sum of the R replicas of a trajectory's counters
@@ -343,6 +375,38 @@ __device__ __forceinline__ float clamp_box(float v, float lo, float hi) {
   if (v < lo) return lo;
   if (v > hi) return hi;
   return v;
+}
+
+// Ascent direction of a MaxCut relaxation at x given acc = (Ax)_v (float32,
+// CSR order) and the weighted degree d: f_B -lambda - 2 acc, f_A -2 acc,
+// f_L 1/2 (d x - acc), f_P 2 ((d x - acc) + lambda x); one rounding per
+// operation, as written (the gradients of Sec. 3's definitions).
+__device__ __forceinline__ float cut_grad(int obj, float lambda_, float x, float acc, int d) {
+  if (obj == OBJ_FB || obj == OBJ_FA) {
+    const float t = 2.0f * acc;
+    return obj == OBJ_FB ? -lambda_ - t : -t;
+  }
+  const float t1 = (float)d * x;
+  const float t2 = t1 - acc;
+  if (obj == OBJ_FL) return 0.5f * t2;
+  const float t3 = lambda_ * x;
+  const float t4 = t2 + t3;
+  return 2.0f * t4;
+}
+
+// Is the binary point fixed at node v under a PGA step of the relaxation?
+// s_v = +1 (z) is fixed iff the gradient there is >= 0, s_v = -1 iff <= 0,
+// with as = (As)_v and d the weighted degree (integers):
+//   f_B: grad = -lambda - 2 as (0 < lambda < 2, integer weights, Thm 3.6)
+//   f_L: grad = 1/2 (d s_v - as);  f_P: grad = 2 (d s_v - as + lambda s_v);
+//   f_A: grad = -2 as.  |as - d| < 2^24, so the f_P comparison is exact in float.
+__device__ __forceinline__ bool cut_fixed(int obj, float lambda_, bool z, int as, int d) {
+  switch (obj) {
+    case OBJ_FL: return z ? (as <= d) : (as >= -d);
+    case OBJ_FP: return z ? ((float)(as - d) <= lambda_) : ((float)(-(as + d)) <= lambda_);
+    case OBJ_FA: return z ? (as <= 0) : (as >= 0);
+    default: return z ? (as <= -1) : (as >= 0);
+  }
 }
 
 // --------------------------------------------------------------------------

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
       }
       const int as = 2 * P - W;
       acc0 += zv ? (W - P) : P;
-      acc1 += !(zv ? (as <= -1) : (as >= 0));
+      acc1 += !(zv ? (as <= -1) : (as >= 0));  // f_B rule (Thm 3.6), any objective
       const int gn = zv ? as : -as;
       acc2 += gn > 0;
       S.gain[e] = gn;

@@ -31,6 +31,8 @@ cudaError_t launch_objective(const SolverDev& S, double* out, cudaStream_t strea
 cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStream_t stream);
 cudaError_t launch_state_init(const SolverDev& S, cudaStream_t stream);
 cudaError_t launch_any_pending(const SolverDev& S, int32_t* out, cudaStream_t stream);
+cudaError_t launch_pool_ctrl(const SolverDev& S, cudaStream_t stream);
+cudaError_t launch_pool_apply(const SolverDev& S, cudaStream_t stream);
 
 // graph-level kernels (autograd path)
 struct HeavyPlan {

@@ -4,6 +4,8 @@
 //   (A x)_vb  = sum over the CSR row of v, in row order, of w_vu x_ub (float32)
 //   grad      = 1 - gamma (A x)_vb              (h, Eq. MIS QUBO)
 //             | -lambda - 2 (A x)_vb            (f_B, Eq. adj_lin_two_props)
+//             | or the gradient of f_L, f_P, f_A (Sec. 3), selected by
+//               `objective`; f_L and f_P also use the weighted degree d_v
 //   V'        = mu V + alpha grad               (momentum ascent, Sec. 5)
 //   x'        = Pi_box(x + V')                  (projection of Sec. 3)
 // and, from the same neighbour gather, the exact evaluation of the rounded
@@ -32,7 +34,7 @@ namespace mqo {
 
 struct StepArgs {
   GraphDev g;
-  int32_t B, Bw, R, problem;
+  int32_t B, Bw, R, problem, objective;
   float alpha, momentum, gamma, lambda_;
   void* X0;
   void* X1;
@@ -64,7 +66,7 @@ __device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float 
   } else {
     const int as = 2 * nb - wsum;
     c0 += z ? (wsum - nb) : nb;
-    const bool fixed = z ? (as <= -1) : (as >= 0);
+    const bool fixed = cut_fixed(a.objective, a.lambda_, z, as, wsum);
     c1 += !fixed;
     const int gn = z ? as : -as;
     c2 += gn > 0;
@@ -74,8 +76,7 @@ __device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float 
     const float tt = a.gamma * acc;
     grad = 1.0f - tt;
   } else {
-    const float tt = 2.0f * acc;
-    grad = -a.lambda_ - tt;
+    grad = cut_grad(a.objective, a.lambda_, x, acc, wsum);
   }
   const float m1 = a.momentum * vold;
   const float m2 = a.alpha * grad;
@@ -569,6 +570,7 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   a.Bw = S.Bw;
   a.R = S.R;
   a.problem = S.p.problem;
+  a.objective = S.p.objective;
   a.alpha = S.p.alpha;
   a.momentum = S.p.momentum;
   a.gamma = S.p.gamma;

@@ -80,14 +80,18 @@ __global__ void k_ctrl(CtrlArgs A) {
     return;
   }
 
-  // fold the previous tick's exact counters (all replicas) and clear them
+  // fold the previous tick's exact counters (all replicas) and clear them;
+  // in pool mode a trajectory that waited last tick keeps its evaluation
+  const bool pool = p.pool_k > 0 && A.mode == CTRL_MACHINE;
   const Counters c = sum_replicas(S.cnt, tau, S.R);
   for (int r = 0; r < S.R; ++r) S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
-  const int64_t cv = (int64_t)c.value;
-  st.ev_value = mis ? cv : cv / 2;
-  st.ev_a = (int64_t)c.a;
-  st.ev_b = (int64_t)c.b;
-  st.last_commits = (int64_t)c.commits;
+  if (!pool || (st.act & ACT_STEP) || st.round != RD_NONE) {
+    const int64_t cv = (int64_t)c.value;
+    st.ev_value = mis ? cv : cv / 2;
+    st.ev_a = (int64_t)c.a;
+    st.ev_b = (int64_t)c.b;
+    st.last_commits = (int64_t)c.commits;
+  }
 
   if (A.mode == CTRL_LS_BEGIN) {
     st.ls_done = 0;
@@ -113,6 +117,89 @@ __global__ void k_ctrl(CtrlArgs A) {
       }
       st.last_round = round;
     }
+  } else if (pool) {
+    // ----- pmQO (Alg. 3/4): the per-trajectory part of the graph's
+    // decision of this tick (k_pool_ctrl) -----
+    const PoolState ps = S.pool[g];
+    const int b = (int)(tau - (int64_t)g * S.B);
+    if (ps.best_src >= 0) {  // the graph's best set was replaced (steps 5, 12, 13)
+      st.best = ps.best;
+      st.accepts += 1;
+    }
+    auto hold = [&](int bits, int64_t value) {
+      act |= bits;
+      st.held = value;
+      st.phase = PH_WAIT;
+    };
+    if (st.phase == PH_WAIT) {
+      if (ps.dec == DEC_NEXT) {  // steps 6-10 from pool member pbase[tau]
+        st.r += 1;
+        st.s = 0;
+        st.phase = PH_DESCENT;
+        reset_keys(p, tau, st.o, st.r, n_g, st);
+        act |= ACT_RESET | ACT_POOL;
+      } else if (ps.dec == DEC_LS) {  // step 13
+        st.held = (int64_t)(-9223372036854775807LL - 1);
+        if (mis ? b == 0 : b < ps.count) {
+          st.phase = PH_LS;
+          act |= mis ? ACT_WORK_BEST : (ACT_WORK_BEST | ACT_POOL);
+          round = RD_COUNT;
+        }
+      } else if (ps.dec == DEC_OUTER) {  // step 2
+        st.held = (int64_t)(-9223372036854775807LL - 1);
+        st.o += 1;
+        st.r = 0;
+        st.s = 0;
+        st.phase = PH_DESCENT;
+        act |= ACT_INIT;
+      }
+    } else if (st.phase == PH_DESCENT) {
+      if (st.s > 0) {
+        const bool pass = mis ? (st.ev_a == 0 && st.ev_b == 0) : (st.ev_a == 0);
+        if (pass) {
+          st.descents += 1;
+          hold(ACT_WORK_ZX, st.ev_value);
+        } else if (st.s >= p.cap) {
+          st.descents += 1;
+          if (mis && p.repair) {
+            st.phase = PH_REPAIR;
+            act |= ACT_WORK_ZX;
+            round = RD_COUNT;
+          } else {
+            // an unrepaired capped MIS point is not a candidate
+            hold(ACT_WORK_ZX, mis ? (int64_t)(-9223372036854775807LL - 1) : st.ev_value);
+          }
+        }
+      }
+    } else if (st.phase == PH_REPAIR) {
+      if (st.ev_a > 0) round = RD_DROP;
+      else if (st.ev_b > 0) round = RD_COMPLETE;
+      else hold(0, st.ev_value);
+    } else if (st.phase == PH_LS) {
+      bool done;
+      if (mis) {
+        if (st.ev_b > 0) { round = RD_COMPLETE; done = false; }
+        else if (!(st.last_round == RD_SWAP && st.last_commits == 0)) { round = RD_SWAP; done = false; }
+        else done = true;
+      } else {
+        if (st.ev_b > 0) { round = RD_FLIP1; done = false; }
+        else if (!(st.last_round == RD_FLIP2 && st.last_commits == 0)) { round = RD_FLIP2; done = false; }
+        else done = true;
+      }
+      if (done) {
+        hold(0, st.ev_value);
+        round = RD_NONE;
+      }
+    }
+    if (st.phase == PH_DESCENT) {
+      act |= ACT_STEP;
+      st.s += 1;
+      st.last_round = RD_NONE;
+      round = RD_NONE;
+    } else if (round != RD_NONE) {
+      st.last_round = round;
+    }
+    st.ticks += 1;
   } else {
     // ----- the machine (same decisions as the oracle's control step) -----
     auto start_outer = [&]() {
@@ -335,8 +422,14 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
       if (src != zb) set_bit_atomic(S.Zbest, v, Bw, b, src);
       zb = src;
     }
+    // pool mode: the base of a reset / local search is pool member pbase[tau]
+    bool base = zb;
+    if (act & ACT_POOL) {
+      const int32_t k = S.pbase[tau];
+      base = k >= 0 && ((S.Pool[v * S.Kw + (k >> 5)] >> (k & 31)) & 1u);
+    }
     if (act & (ACT_WORK_ZX | ACT_WORK_BEST)) {
-      const bool wv = (act & ACT_WORK_ZX) ? get_bit(Zp, v, Bw, b) : zb;
+      const bool wv = (act & ACT_WORK_ZX) ? get_bit(Zp, v, Bw, b) : base;
       set_bit_atomic(S.Zwork, v, Bw, b, wv);
     }
     if (act & (ACT_RESET | ACT_INIT)) {
@@ -344,7 +437,7 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
       float x;
       if (act & ACT_RESET) {
         const TrajState& st = S.st[tau];
-        x = zb ? 1.0f : (mis ? 0.0f : -1.0f);
+        x = base ? 1.0f : (mis ? 0.0f : -1.0f);
         uint32_t keys[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) keys[i] = st.rkeys[i];
@@ -582,7 +675,7 @@ __global__ void __launch_bounds__(kPairThreads) k_disc(SolverDev S, int pass) {
         }
         const int as = 2 * P - W;
         acc0 += zv ? (W - P) : P;
-        const bool fixed = zv ? (as <= -1) : (as >= 0);
+        const bool fixed = zv ? (as <= -1) : (as >= 0);  // f_B rule (Thm 3.6), any objective
         acc1 += !fixed;
         const int gn = zv ? as : -as;
         acc2 += gn > 0;
@@ -704,8 +797,9 @@ cudaError_t launch_counters_out(const SolverDev& S, const Counters* c, int64_t* 
 }
 
 // relaxed objective per trajectory in double: (Ax)_v in float32 (CSR order),
-// then x_v and x_v*(Ax)_v accumulated in double per thread, reduced per
-// item in shared memory
+// then the node's terms in double (MIS h; MaxCut f_B, f_L = 1/4 x'(D-A)x,
+// f_P = x'(D-A+lambda I)x or f_A = -x'Ax), accumulated per thread and
+// reduced per item in shared memory
 __global__ void __launch_bounds__(kPairThreads) k_objective(SolverDev S, double* out) {
   __shared__ double s_obj[128];
   const int64_t t = *S.tick;
@@ -724,13 +818,27 @@ __global__ void __launch_bounds__(kPairThreads) k_objective(SolverDev S, double*
   item_pairs(S, item, [&](const PairCtx& c) {
     if (!c.in) return;
     float acc = 0.0f;
+    int d = 0;
     for (int32_t j = S.g.row_ptr[c.v]; j < S.g.row_ptr[c.v + 1]; ++j) {
       const float xu = ld((int64_t)S.g.col[j] * B + c.b);
-      if (S.g.w == nullptr || S.g.w[j] >= 0) acc = acc + xu;
+      const int w = S.g.w == nullptr ? 1 : (int)S.g.w[j];
+      d += w;
+      if (w >= 0) acc = acc + xu;
       else acc = acc - xu;
     }
     const double xv = (double)ld(c.v * B + c.b);
-    part += mis ? xv - 0.5 * (double)S.p.gamma * xv * (double)acc : -(double)S.p.lambda_ * xv - xv * (double)acc;
+    const double xax = xv * (double)acc, lam = (double)S.p.lambda_;
+    if (mis) {
+      part += xv - 0.5 * (double)S.p.gamma * xax;
+    } else {
+      const double xdx = (double)d * xv * xv;
+      switch (S.p.objective) {
+        case OBJ_FL: part += 0.25 * (xdx - xax); break;
+        case OBJ_FP: part += (xdx - xax) + lam * xv * xv; break;
+        case OBJ_FA: part += -xax; break;
+        default: part += -lam * xv - xax; break;
+      }
+    }
   });
   if (part != 0.0) atomicAdd(&s_obj[threadIdx.x % B], part);
   __syncthreads();
@@ -783,7 +891,20 @@ __global__ void k_state_init(SolverDev S) {
     st.ls_done = 0;
     for (int i = 0; i < 6; ++i) st.rkeys[i] = 0u;
     st.rk = 0;
+    st.held = (int64_t)(-9223372036854775807LL - 1);
     S.st[tau] = st;
+    if (S.K > 0 && tau < S.g.num_graphs) {
+      PoolState ps;
+      ps.epoch = EP_DESCENT;
+      ps.count = 0;
+      ps.best = st.best;
+      ps.merges = 0;
+      ps.dec = DEC_NONE;
+      ps.best_src = -1;
+      ps.merged = 0;
+      ps.stamp = 0;
+      S.pool[tau] = ps;
+    }
     S.act[tau] = ACT_INIT;
     S.rnd[tau] = RD_NONE;
     S.bestv[tau] = st.best;

@@ -56,7 +56,8 @@ def okw(p):
     return oracle.params(problem=p.problem, batch=p.batch, x_dtype=p.x_dtype, v_dtype=p.v_dtype, alpha=p.alpha,
                          momentum=p.momentum, gamma=p.gamma, lambda_=p.lambda_, rho=p.rho, sigma=p.sigma,
                          t_gs=p.t_gs, descent_cap=p.descent_cap, init_kind=p.init_kind,
-                         local_search=p.local_search, repair=p.repair, seed=p.seed)
+                         local_search=p.local_search, repair=p.repair, seed=p.seed, objective=p.objective,
+                         pool_k=p.pool_k)
 
 
 def oracle_graphs(G):
