@@ -1102,8 +1102,11 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
         plans.push_back({st, 0, 0, dc});
         if (wide_ok) plans.push_back({st, 0, 1, dc});
       } else {
-        for (int v : {1, 2, 4})
+        for (int v : {1, 2, 4, 8}) {
+          // 16-byte lanes (8 trajectories) only for 16-bit x and momentum
+          if (v == 8 && (S.p.x_dtype == DT_F32 || S.p.v_dtype == DT_F32)) continue;
           if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc});
+        }
       }
     }
   const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem};

@@ -371,6 +371,39 @@ __device__ __forceinline__ void add_f32x2(float& a, float& b, float x, float y) 
       : "f"(x), "f"(y));
 }
 
+// acc[e] += widened bfloat16 e of the VEC-element row at p (8 or 16 bytes,
+// aligned), one add.rn.f32.bf16 (sm_100 family) per element: the bfloat16
+// operand converts to float32 exactly and the sum rounds once to nearest,
+// bit-identical to widening first and adding in float32.
+__device__ __forceinline__ void add_bf16x2_word(float& a, float& b, uint32_t w) {
+  asm("{\n\t.reg .b16 lo, hi;\n\t"
+      "mov.b32 {lo, hi}, %2;\n\t"
+      "add.rn.f32.bf16 %0, lo, %0;\n\t"
+      "add.rn.f32.bf16 %1, hi, %1;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "r"(w));
+}
+template <int VEC>
+__device__ __forceinline__ void add_bf16_row(float* acc, const unsigned char* p);
+template <>
+__device__ __forceinline__ void add_bf16_row<4>(float* acc, const unsigned char* p) {
+  const uint2 r = *reinterpret_cast<const uint2*>(p);
+  add_bf16x2_word(acc[0], acc[1], r.x);
+  add_bf16x2_word(acc[2], acc[3], r.y);
+}
+template <>
+__device__ __forceinline__ void add_bf16_row<8>(float* acc, const unsigned char* p) {
+  const uint4 r = *reinterpret_cast<const uint4*>(p);
+  add_bf16x2_word(acc[0], acc[1], r.x);
+  add_bf16x2_word(acc[2], acc[3], r.y);
+  add_bf16x2_word(acc[4], acc[5], r.z);
+  add_bf16x2_word(acc[6], acc[7], r.w);
+}
+template <>
+__device__ __forceinline__ void add_bf16_row<2>(float* acc, const unsigned char* p) {
+  add_bf16x2_word(acc[0], acc[1], *reinterpret_cast<const uint32_t*>(p));
+}
+
 __device__ __forceinline__ float clamp_box(float v, float lo, float hi) {
   if (v < lo) return lo;
   if (v > hi) return hi;

@@ -31,6 +31,9 @@ __device__ __forceinline__ bool sbit(const uint32_t* words, int u, int Bw, int b
 // are independent, so one list costs one memory latency; longer rows keep
 // their tail (entries past rs + 32 kNb) in memory.
 constexpr int kNb = 5;
+// tight neighbours a set node keeps in registers for its swap search; a
+// longer list falls back to the sequential scan
+constexpr int kTight = 8;
 
 struct NbList {
   int32_t u[kNb];
@@ -146,6 +149,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   const bool w_comp = __any_sync(0xffffffffu, round == RD_COMPLETE);
   const bool w_flip = __any_sync(0xffffffffu, round == RD_FLIP1);
   const bool w_lane = __any_sync(0xffffffffu, round == RD_SWAP || round == RD_FLIP2);
+  const bool w_swap = __any_sync(0xffffffffu, round == RD_SWAP);
   const bool w_words = w_drop || w_comp || w_flip;
   const bool w_act = __any_sync(0xffffffffu, round != RD_NONE);
   const int vfirst = warp / Bw;
@@ -180,28 +184,65 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
       if (mc) sW[vl * Bw + wk] ^= mc;  // complete sets clear bits, flip1 toggles
     }
     acc3 += dropv + addv + flipv;
-    if (round == RD_SWAP) {
+    if (w_swap) {
+      // (1,2)-swap proposal of a set node v (Def. 2.3): the first pair, in
+      // CSR order of N(v), of non-adjacent tight neighbours.  The warp first
+      // lists each lane's tight neighbours together: a 32-entry chunk of
+      // N(v) is loaded at once, and only entries whose tight word has a bit
+      // of a proposing lane are broadcast; the pairs of the (short) lists
+      // are then tested per lane.
+      const unsigned need = __ballot_sync(0xffffffffu, round == RD_SWAP && zv);
       int32_t fa = -1, fb = -1;
-      if (zv) {
-        for (int32_t i = rs; i < re && fa < 0; ++i) {
-          const int32_t a = col[i];
-          if (!sbit(sA, a - off, Bw, b)) continue;
-          for (int32_t j = i + 1; j < re; ++j) {
-            const int32_t cc = col[j];
-            if (!sbit(sA, cc - off, Bw, b)) continue;
-            if (!sorted_contains(col, rp[a], rp[a + 1], cc)) {
-              fa = a;
-              fb = cc;
-              break;
+      if (need) {
+        int32_t tl[kTight];
+        int ntl = 0;
+        for (int32_t c0 = rs; c0 < re; c0 += 32) {
+          const int32_t j = c0 + lane;
+          const int32_t u = j < re ? col[j] : -1;
+          const uint32_t tw = u >= 0 ? sA[(u - off) * Bw + wk] & need : 0u;
+          unsigned m = __ballot_sync(0xffffffffu, tw != 0u);
+          while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            const int32_t uu = __shfl_sync(0xffffffffu, u, i);
+            const uint32_t ww = __shfl_sync(0xffffffffu, tw, i);
+            if (ww & bit) {
+              if (ntl < kTight) tl[ntl] = uu;
+              ++ntl;
+            }
+          }
+        }
+        if ((need & bit) && ntl <= kTight) {
+          for (int x = 0; x < ntl && fa < 0; ++x)
+            for (int y = x + 1; y < ntl; ++y)
+              if (!sorted_contains(col, rp[tl[x]], rp[tl[x] + 1], tl[y])) {
+                fa = tl[x];
+                fb = tl[y];
+                break;
+              }
+        } else if (need & bit) {  // a long tight list: the sequential scan
+          for (int32_t i = rs; i < re && fa < 0; ++i) {
+            const int32_t a = col[i];
+            if (!sbit(sA, a - off, Bw, b)) continue;
+            for (int32_t j = i + 1; j < re; ++j) {
+              const int32_t cc = col[j];
+              if (!sbit(sA, cc - off, Bw, b)) continue;
+              if (!sorted_contains(col, rp[a], rp[a + 1], cc)) {
+                fa = a;
+                fb = cc;
+                break;
+              }
             }
           }
         }
       }
-      S.pa[e] = fa;
-      S.pb[e] = fb;
-      if (fa >= 0) {
-        S.owner[(int64_t)fa * B + b] = (int32_t)v;
-        S.owner[(int64_t)fb * B + b] = (int32_t)v;
+      if (round == RD_SWAP) {
+        S.pa[e] = fa;
+        S.pb[e] = fb;
+        if (fa >= 0) {
+          S.owner[(int64_t)fa * B + b] = (int32_t)v;
+          S.owner[(int64_t)fb * B + b] = (int32_t)v;
+        }
       }
     }
     if (round == RD_FLIP2) {

@@ -27,6 +27,8 @@
 //   shared memory; every neighbour gather then hits shared memory, and the
 //   MIS checker ORs whole 32-trajectory words of neighbour bits.  Several
 //   rows per warp share each shuffle and shared-memory instruction.
+#include <type_traits>
+
 #include "mqo_dev.cuh"
 #include "mqo_host.h"
 
@@ -131,16 +133,40 @@ __device__ __forceinline__ void flush_step_counters(const StepArgs& a, unsigned 
 }
 
 // ---------------------------------------------------------------- generic
+// The CTA first stages its item's row pointers and (up to kColCap) column
+// indices / weights in shared memory with coalesced loads, so that a row's
+// neighbour ids cost no dependent global load; each row then issues the
+// loads of its own x and V and of up to kGather neighbour rows of x before
+// consuming any of them.  A row group of LPR = B/VEC lanes owns one node.
+constexpr int kColCap = 4096;  // staged column indices per item
+constexpr int kGather = 4;     // neighbour rows of x in flight per row group
+
 template <typename TX, typename TV, int VEC>
-__global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
+__global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) {
   __shared__ unsigned long long s_cnt[3 * 128];
+  __shared__ int32_t s_rp[kItemMaxNodes + 1];
+  __shared__ int32_t s_col[kColCap];
+  __shared__ int8_t s_w[kColCap];
   const int it = blockIdx.x;
   const Item item = a.g.items[it];
   const int g = item.g;
   const int64_t t = *a.tick;
   if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
   const int B = a.B;
+  const bool weighted = a.g.w != nullptr;
+  const int32_t* __restrict__ rp = a.g.row_ptr;
+  const int32_t* __restrict__ col = a.g.col;
+  const int8_t* __restrict__ wts = a.g.w;
+  const int nrows = item.v1 - item.v0;
   for (int i = threadIdx.x; i < 3 * B; i += blockDim.x) s_cnt[i] = 0ull;
+  for (int i = threadIdx.x; i <= nrows; i += blockDim.x) s_rp[i] = rp[item.v0 + i];
+  __syncthreads();
+  const int32_t j0 = s_rp[0];
+  const int32_t ncol = min(s_rp[nrows] - j0, kColCap);
+  for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+    s_col[i] = __ldcs(col + j0 + i);
+    if (weighted) s_w[i] = wts[j0 + i];
+  }
   __syncthreads();
 
   const int lpr = B / VEC;
@@ -154,14 +180,10 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
   const bool mis = a.problem == PROB_MIS;
   const float thr = mis ? 0.5f : 0.0f;
   const float lo = mis ? 0.0f : -1.0f;
-  const bool weighted = a.g.w != nullptr;
   const TX* __restrict__ Xc = static_cast<const TX*>((t & 1) ? a.X1 : a.X0);
   TX* __restrict__ Xn = static_cast<TX*>((t & 1) ? a.X0 : a.X1);
   uint32_t* __restrict__ Zn = (t & 1) ? a.ZX0 : a.ZX1;
   TV* __restrict__ V = static_cast<TV*>(a.V);
-  const int32_t* __restrict__ rp = a.g.row_ptr;
-  const int32_t* __restrict__ col = a.g.col;
-  const int8_t* __restrict__ wts = a.g.w;
   const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;  // lanes sharing one output bit word
   const unsigned rmask = lpr == 32 ? 0xffffffffu : (((1u << lpr) - 1u) << (sub * lpr));
 
@@ -173,7 +195,8 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
 #pragma unroll
   for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
 
-  for (int v = item.v0 + warp * rpw + sub; v < item.v1; v += nwarps * rpw) {
+  for (int vr = warp * rpw + sub; vr < nrows; vr += nwarps * rpw) {
+    const int v = item.v0 + vr;
     const int64_t base = (int64_t)v * B + b0;
     const Pack<TX, VEC> xv = ld_pack<TX, VEC>(Xc + base);
     const Pack<TV, VEC> vv = ld_pack_stream<TV, VEC>(V + base);
@@ -181,45 +204,30 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
     int pos[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
-    const int rs = rp[v], re = rp[v + 1];
+    const int rs = s_rp[vr], re = s_rp[vr + 1];
     int wsum = 0;
-    for (int cb = rs; cb < re; cb += lpr) {
-      const int j = cb + l;
-      const int myu = j < re ? __ldcs(col + j) : 0;
-      const int myw = (weighted && j < re) ? (int)wts[j] : 1;
-      const int cnt = min(lpr, re - cb);
-      int k = 0;
-      for (; k + 8 <= cnt; k += 8) {
-        int u[8], w[8];
-        Pack<TX, VEC> p[8];
+    for (int j = rs; j < re; j += kGather) {
+      int u[kGather], w[kGather];
+      Pack<TX, VEC> p[kGather];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          u[q] = __shfl_sync(rmask, myu, k + q, lpr);
-          w[q] = weighted ? __shfl_sync(rmask, myw, k + q, lpr) : 1;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) p[q] = ld_pack<TX, VEC>(Xc + (int64_t)u[q] * B + b0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          wsum += w[q];
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            const float f = to_f(p[q].e[e]);
-            acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
-            pos[e] += (f > thr) ? w[q] : 0;
-          }
-        }
+      for (int q = 0; q < kGather; ++q) {
+        const int jj = j + q;
+        const int r = jj - j0;
+        const bool in = jj < re;
+        u[q] = in ? (r < ncol ? s_col[r] : col[jj]) : v;  // past the row: a harmless load of v's own row
+        w[q] = in ? (weighted ? (int)(r < ncol ? s_w[r] : wts[jj]) : 1) : 0;
       }
-      for (; k < cnt; ++k) {
-        const int u = __shfl_sync(rmask, myu, k, lpr);
-        const int w = weighted ? __shfl_sync(rmask, myw, k, lpr) : 1;
-        const Pack<TX, VEC> p = ld_pack<TX, VEC>(Xc + (int64_t)u * B + b0);
-        wsum += w;
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) p[q] = ld_pack<TX, VEC>(Xc + (int64_t)u[q] * B + b0);
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) {
+        if (j + q >= re) break;
+        wsum += w[q];
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-          const float f = to_f(p.e[e]);
-          acc[e] = w >= 0 ? acc[e] + f : acc[e] - f;
-          pos[e] += (f > thr) ? w : 0;
+          const float f = to_f(p[q].e[e]);
+          acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
+          pos[e] += (f > thr) ? w[q] : 0;
         }
       }
     }
@@ -230,8 +238,7 @@ __global__ void __launch_bounds__(256) k_step_g(StepArgs a) {
     for (int e = 0; e < VEC; ++e) {
       bool zn;
       step_element<TX, TV>(a, mis, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, (stepm >> e) & 1u, xo.e[e],
-                           vo.e[e],
-                           zn, c0[e], c1[e], c2[e]);
+                           vo.e[e], zn, c0[e], c1[e], c2[e]);
       zbits |= (unsigned)zn << e;
     }
     st_pack<TX, VEC>(Xn + base, xo);
@@ -401,6 +408,13 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
 #pragma unroll
         for (int k = 0; k < LPR; ++k) {
           const int o = __shfl_sync(0xffffffffu, myo[c], k, LPR);
+          if constexpr (MIS && std::is_same<TX, __nv_bfloat16>::value) {
+            // one mixed-precision add per trajectory: the bfloat16 operand is
+            // widened exactly inside the add, which rounds once (RN), so the
+            // sums are those of the widened values added one by one
+            add_bf16_row<VEC>(acc, sXl + o);
+            continue;
+          }
           float f[VEC];
           load_unpack<TX, VEC>(sXl + o, f);
           if (weighted) {
@@ -546,7 +560,7 @@ bool step_wide_possible(int B, int x_dtype) { return x_dtype != DT_F32 ? (B == 3
 
 template <typename TX, typename TV, int VEC>
 static cudaError_t launch_vec(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step_g<TX, TV, VEC><<<grid, 256, 0, s>>>(a);
+  k_step_g<TX, TV, VEC><<<grid, 512, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -558,6 +572,9 @@ static cudaError_t launch_tv(int vec, bool smem_path, bool wide, size_t smem, bo
     case 1: return launch_vec<TX, TV, 1>(a, grid, s);
     case 2: return launch_vec<TX, TV, 2>(a, grid, s);
     case 4: return launch_vec<TX, TV, 4>(a, grid, s);
+    case 8:
+      if constexpr (sizeof(TX) == 2 && sizeof(TV) == 2) return launch_vec<TX, TV, 8>(a, grid, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

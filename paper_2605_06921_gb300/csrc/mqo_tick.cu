@@ -36,11 +36,10 @@ __device__ __forceinline__ void reset_keys(const Params& p, int64_t tau, int32_t
   st.rk = (int64_t)floor(p.rho * (double)n_g);
 }
 
-__global__ void k_ctrl(CtrlArgs A) {
+// The control step of trajectory tau; c = its counters of the previous tick
+// (all replicas summed; not used by a forced reset).
+__device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const Counters& c) {
   const SolverDev& S = A.S;
-  const int64_t T = (int64_t)S.g.num_graphs * S.B;
-  const int64_t tau = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tau >= T) return;
   const int64_t t = *S.tick;
   const int g = (int)(tau / S.B);
   const int32_t n_g = S.g.node_off[g + 1] - S.g.node_off[g];
@@ -80,11 +79,10 @@ __global__ void k_ctrl(CtrlArgs A) {
     return;
   }
 
-  // fold the previous tick's exact counters (all replicas) and clear them;
-  // in pool mode a trajectory that waited last tick keeps its evaluation
+  // fold the previous tick's exact counters (summed and cleared by the
+  // caller); in pool mode a trajectory that waited last tick keeps its
+  // evaluation
   const bool pool = p.pool_k > 0 && A.mode == CTRL_MACHINE;
-  const Counters c = sum_replicas(S.cnt, tau, S.R);
-  for (int r = 0; r < S.R; ++r) S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
   if (!pool || (st.act & ACT_STEP) || st.round != RD_NONE) {
     const int64_t cv = (int64_t)c.value;
     st.ev_value = mis ? cv : cv / 2;
@@ -305,10 +303,53 @@ __global__ void k_ctrl(CtrlArgs A) {
   }
 }
 
+// one thread per trajectory: few counter replicas
+__global__ void k_ctrl(CtrlArgs A) {
+  const SolverDev& S = A.S;
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  const int64_t tau = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tau >= T) return;
+  Counters c{0ull, 0ull, 0ull, 0ull};
+  if (A.mode != CTRL_RESET) {  // a forced reset leaves the counters in place
+    c = sum_replicas(S.cnt, tau, S.R);
+    for (int r = 0; r < S.R; ++r) S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
+  }
+  ctrl_one(A, tau, c);
+}
+
+// one warp per trajectory: the lanes sum and clear the R replicas together
+__global__ void k_ctrl_w(CtrlArgs A) {
+  const SolverDev& S = A.S;
+  const int64_t T = (int64_t)S.g.num_graphs * S.B;
+  const int64_t tau = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (tau >= T) return;
+  Counters c{0ull, 0ull, 0ull, 0ull};
+  if (A.mode != CTRL_RESET) {
+    for (int r = lane; r < S.R; r += 32) {
+      const Counters x = S.cnt[tau * S.R + r];
+      c.value += x.value;
+      c.a += x.a;
+      c.b += x.b;
+      c.commits += x.commits;
+      S.cnt[tau * S.R + r] = Counters{0ull, 0ull, 0ull, 0ull};
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c.value += __shfl_xor_sync(0xffffffffu, c.value, o);
+      c.a += __shfl_xor_sync(0xffffffffu, c.a, o);
+      c.b += __shfl_xor_sync(0xffffffffu, c.b, o);
+      c.commits += __shfl_xor_sync(0xffffffffu, c.commits, o);
+    }
+  }
+  if (lane == 0) ctrl_one(A, tau, c);
+}
+
 cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream) {
   const int64_t T = (int64_t)S.g.num_graphs * S.B;
   CtrlArgs a{S, mode, mask};
-  k_ctrl<<<(unsigned)((T + 127) / 128), 128, 0, stream>>>(a);
+  if (S.R >= 8) k_ctrl_w<<<(unsigned)((T * 32 + 255) / 256), 256, 0, stream>>>(a);
+  else k_ctrl<<<(unsigned)((T + 127) / 128), 128, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
