@@ -52,6 +52,12 @@ WORKLOADS = {
 }
 
 
+# the differentiable f_B objective (torch.autograd.Function with the fused
+# SpMM backward) driven by the projected momentum kernel
+AUTOGRAD = dict(desc="f_B autograd: Chung-Lu power law (exponent 2.5, mean degree 8) n=1e6, B=64 FP32, "
+                     "forward + backward + projected momentum step", batch=64, lambda_=0.001, lr=0.001, momentum=0.9)
+
+
 def make_graph(name):
     if name == "mis_batched":
         return mi.workload_mis_batched()
@@ -59,6 +65,8 @@ def make_graph(name):
         return mi.workload_maxcut_regular()
     if name == "mis_scale":
         return mi.workload_mis_scale()
+    if name == "autograd_powerlaw":
+        return mi.workload_chung_lu()
     raise ValueError(name)
 
 
@@ -170,6 +178,25 @@ def reference_arm(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+    return 0
+
+
+def reference_autograd(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    wl = AUTOGRAD
+    G = make_graph("autograd_powerlaw")
+    vals = [oracle_autograd_sample(G, wl["batch"], wl["lambda_"], target_s=max(1.0, 60.0 / max(args.steps, 1)))
+            for _ in range(args.steps)]
+    value = statistics.median(v["value"] for v in vals)
+    eu_step = 2.0 * G.nnz * wl["batch"]
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": eu_step / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "nnz": G.nnz, "batch": wl["batch"]},
+        "cpu_baseline": dict(vals[-1], value=value),
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
     return 0
 
 
@@ -465,13 +492,172 @@ def gpu_arm(args):
     return 0
 
 
+def fb_kernel_bytes(G, B):
+    """col + row_ptr read once, X read once, the gradient written once."""
+    return G.nnz * 4 + (G.n + 1) * 4 + 2 * G.n * B * 4
+
+
+def oracle_autograd_sample(G, B, lam, target_s=12.0, cores=None):
+    """The oracle's float64 f_B and gradient, column by column, on a bounded
+    number of the workload's columns (two edge passes per column)."""
+    cores = cores or os.cpu_count() or 1
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    _autograd_job((G.row_ptr, G.col_idx, G.n, lam, 0))
+    per_col = time.perf_counter() - t0
+    cols = int(min(B, max(cores, target_s * cores / max(per_col, 1e-9))))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(min(cores, cols)) as pool:
+        pool.map(_autograd_job, [(G.row_ptr, G.col_idx, G.n, lam, c) for c in range(cols)], chunksize=1)
+    wall = time.perf_counter() - t0
+    eu = 2.0 * G.nnz * cols
+    del rng
+    return dict(value=eu / wall, unit=UNIT, cores=min(cores, cols), kind="oracle",
+                sample=f"{cols} of the {B} columns (float64 objective + gradient per column), "
+                       f"{eu:.3e} edge-updates in {wall:.2f} s wall")
+
+
+def _autograd_job(args):
+    rp, col, n, lam, c = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    og = oracle.Graph(mi.Graph(n, rp, col, None))
+    x = np.random.default_rng(100 + c).random(n) * 2.0 - 1.0
+    oracle.objective_f64(og, 1, 0.0, lam, x)
+    oracle.gradient_f64(og, 1, 0.0, lam, x)
+    return c
+
+
+def autograd_arm(args):
+    import torch
+    import paper_2605_06921_gb300 as mq
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = AUTOGRAD
+    G = make_graph("autograd_powerlaw")
+    B, lam = wl["batch"], wl["lambda_"]
+    g = mq.Graph(G)
+    gen = torch.Generator(device="cuda").manual_seed(1000 * rank)
+    X = (torch.rand((G.n, B), device="cuda", generator=gen) * 2 - 1).requires_grad_(True)
+    opt = mq.PGAMomentum([X], lr=wl["lr"], momentum=wl["momentum"])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ph = {"forward": 0.0, "backward": 0.0, "optimizer": 0.0}
+
+    def step(timed):
+        opt.zero_grad(set_to_none=False)
+        if timed:
+            ev[0].record()
+        obj = mq.FbObjective.apply(X, g, lam)
+        if timed:
+            ev[1].record()
+        obj.sum().backward()
+        if timed:
+            ev[2].record()
+        opt.step()
+        if timed:
+            ev[3].record()
+        return obj
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize()
+        ph["forward"] += ev[0].elapsed_time(ev[1])
+        ph["backward"] += ev[1].elapsed_time(ev[2])
+        ph["optimizer"] += ev[2].elapsed_time(ev[3])
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    sampler.__exit__()
+    clocks = sampler.summary()
+    ms_total = e0.elapsed_time(e1)
+    eu_step = 2.0 * G.nnz * B
+    ms, value = aggregate_ranks(ms_total, eu_step * args.steps, dist, "cuda")
+    # forward and backward: one launch for rows of <= 512 entries and row
+    # chunks, one more if some row is longer; the momentum step: one
+    per_fb = 1 + int(G.degrees().max() > 512)
+    launches_per_step = 2 * per_fb + 1
+    bwd_ms = ph["backward"] / args.steps
+    alg = fb_kernel_bytes(G, B)
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg / (bwd_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "mqo::k_fb_units (f_B backward, fused SpMM gradient)",
+            "algorithmic_bytes_per_launch": alg, "backward_ms": bwd_ms,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    # end to end through the public API: X copied from pinned host memory
+    # every step, forward + backward + optimiser step, the objective read back
+    Xh = X.detach().cpu().pin_memory()
+    Xe = torch.empty_like(X).requires_grad_(True)
+    opt_e = mq.PGAMomentum([Xe], lr=wl["lr"], momentum=wl["momentum"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.no_grad():
+            Xe.copy_(Xh, non_blocking=True)
+        opt_e.zero_grad(set_to_none=False)
+        obj = mq.FbObjective.apply(Xe, g, lam)
+        obj.sum().backward()
+        opt_e.step()
+        obj.detach().cpu()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    ms_e2e, e2e_value = aggregate_ranks(t_e2e * 1e3, eu_step * args.steps, dist, "cuda")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_autograd_sample(G, B, lam)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "nnz": G.nnz, "nodes": G.n, "batch": B,
+                       "edge_updates_per_step": eu_step, "l2": "inputs larger than L2 (X 256 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": G.n * B * 4,
+                    "d2h_bytes_per_step": B * 8},
+            "gpu_launches": launches_per_step * args.steps,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in ph.items()},
+            "clocks": clocks,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="mis_batched", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="mis_batched", choices=sorted(WORKLOADS) + ["autograd_powerlaw"])
     ap.add_argument("--x-dtype", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--v-dtype", default=None, choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu", action="store_true")
@@ -483,7 +669,11 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
+        if args.workload == "autograd_powerlaw":
+            return reference_autograd(args)
         return reference_arm(args)
+    if args.workload == "autograd_powerlaw":
+        return autograd_arm(args)
     return gpu_arm(args)
 
 

@@ -37,7 +37,7 @@ mqo_status fail(mqo_status st, const char* fmt, ...) {
 constexpr int kChunkNodes = kItemMaxNodes;  // nodes per item
 constexpr int kSplit = 512;       // row length above which the f_B kernels chunk a row
 constexpr size_t kStepSmemLimit = 110 * 1024;  // shared-memory step kernel if the graph block fits
-constexpr size_t kDiscSmemLimit = 96 * 1024;   // fused discrete kernel if the graph's bit words fit
+constexpr size_t kDiscSmemLimit = 160 * 1024;  // fused discrete kernel if the graph's bit words fit
 
 }  // namespace
 

@@ -20,7 +20,7 @@ namespace mqo {
 
 namespace {
 
-constexpr int kDgThreads = 512;
+constexpr int kDgThreads = 1024;  // one CTA per SM: 32 warps overlap their neighbour-list loads
 
 __device__ __forceinline__ bool sbit(const uint32_t* words, int u, int Bw, int b) {
   return (words[u * Bw + (b >> 5)] >> (b & 31)) & 1u;
@@ -268,55 +268,63 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   __syncthreads();
 
   // ---------------- pass B: commits
+  // A proposal commits if no neighbour of its two new nodes (swap) or of
+  // its two flipped nodes (2-flip) is claimed by a smaller proposer.  The
+  // warp checks one proposing lane at a time, its 32 lanes scanning the two
+  // neighbour lists together.
+  const bool w_flip2 = __any_sync(0xffffffffu, round == RD_FLIP2);
   for (int vl = vfirst; (w_drop || w_lane) && vl < ng; vl += vstep) {
     const int64_t v = off + vl;
     const int64_t e = v * B + b;
     const unsigned md = sD[vl * Bw + wk];
     if (lane == 0 && md) atomicAnd(&sW[vl * Bw + wk], ~md);
-    if (round == RD_SWAP) {
-      const int32_t fa = S.pa[e];
-      if (fa >= 0) {
-        const int32_t fb = S.pb[e];
-        bool ok = true;
-        const int32_t ends[2] = {fa, fb};
-        for (int k = 0; k < 2 && ok; ++k) {
-          const int32_t x = ends[k];
-          for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
-            if (S.owner[(int64_t)col[j] * B + b] < (int32_t)v) {
-              ok = false;
-              break;
-            }
-          }
-        }
-        if (ok) {
-          atomicAnd(&sW[vl * Bw + wk], ~bit);
-          atomicOr(&sW[(fa - off) * Bw + wk], bit);
-          atomicOr(&sW[(fb - off) * Bw + wk], bit);
-          acc3 += 1;
-        }
+    if (w_swap) {
+      const int32_t fa = round == RD_SWAP ? S.pa[e] : -1;
+      const int32_t fb = fa >= 0 ? S.pb[e] : -1;
+      bool ok = false;
+      unsigned pm = __ballot_sync(0xffffffffu, fa >= 0);
+      while (pm) {
+        const int i = __ffs(pm) - 1;
+        pm &= pm - 1u;
+        const int32_t ends[2] = {__shfl_sync(0xffffffffu, fa, i), __shfl_sync(0xffffffffu, fb, i)};
+        const int bi = wk * 32 + i;
+        bool bad = false;
+        for (int k = 0; k < 2; ++k)
+          for (int32_t j = rp[ends[k]] + lane; j < rp[ends[k] + 1]; j += 32)
+            bad |= S.owner[(int64_t)col[j] * B + bi] < (int32_t)v;
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == i) ok = !bad;
+      }
+      if (fa >= 0 && ok) {
+        atomicAnd(&sW[vl * Bw + wk], ~bit);
+        atomicOr(&sW[(fa - off) * Bw + wk], bit);
+        atomicOr(&sW[(fb - off) * Bw + wk], bit);
+        acc3 += 1;
       }
     }
-    if (round == RD_FLIP2) {
-      const int32_t fb = S.pb[e];
-      if (fb >= 0) {
-        bool ok = S.owner[e] == (int32_t)v && S.owner[(int64_t)fb * B + b] == (int32_t)v;
-        const int32_t ends[2] = {(int32_t)v, fb};
-        for (int k = 0; k < 2 && ok; ++k) {
-          const int32_t x = ends[k];
-          for (int32_t j = rp[x]; j < rp[x + 1]; ++j) {
+    if (w_flip2) {
+      const int32_t fb = round == RD_FLIP2 ? S.pb[e] : -1;
+      bool ok = fb >= 0 && S.owner[e] == (int32_t)v && S.owner[(int64_t)fb * B + b] == (int32_t)v;
+      unsigned pm = __ballot_sync(0xffffffffu, ok);
+      while (pm) {
+        const int i = __ffs(pm) - 1;
+        pm &= pm - 1u;
+        const int32_t f = __shfl_sync(0xffffffffu, fb, i);
+        const int32_t ends[2] = {(int32_t)v, f};
+        const int bi = wk * 32 + i;
+        bool bad = false;
+        for (int k = 0; k < 2; ++k)
+          for (int32_t j = rp[ends[k]] + lane; j < rp[ends[k] + 1]; j += 32) {
             const int32_t y = col[j];
-            if (y == (int32_t)v || y == fb) continue;
-            if (S.owner[(int64_t)y * B + b] < (int32_t)v) {
-              ok = false;
-              break;
-            }
+            if (y != (int32_t)v && y != f) bad |= S.owner[(int64_t)y * B + bi] < (int32_t)v;
           }
-        }
-        if (ok) {
-          atomicXor(&sW[vl * Bw + wk], bit);
-          atomicXor(&sW[(fb - off) * Bw + wk], bit);
-          acc3 += 1;
-        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == i) ok = !bad;
+      }
+      if (ok) {
+        atomicXor(&sW[vl * Bw + wk], bit);
+        atomicXor(&sW[(fb - off) * Bw + wk], bit);
+        acc3 += 1;
       }
     }
   }
