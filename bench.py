@@ -283,11 +283,11 @@ def algorithmic_bytes_per_step(G, B, sx, sv):
     return G.nnz * 4 + (n + 1) * 4 + 2 * n * B * sx + 2 * n * B * sv + n * bw * 4
 
 
-def step_kernel_traffic(workload, x_dtype, variant):
-    """Per-launch DRAM bytes of the step kernel variant (smem, smem_wide,
-    global) from the committed ncu summary, or None if there is none or the
-    kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}_{x_dtype}.txt")
+def profile_traffic(name, variant, sources):
+    """Per-launch DRAM bytes of a kernel variant from the committed ncu
+    summary profiles/<name>.txt, or None if there is none or the kernel
+    sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{name}.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -296,11 +296,16 @@ def step_kernel_traffic(workload, x_dtype, variant):
     if not m or not t:
         return None
     h = hashlib.sha256()
-    for f in ("mqo_step.cu", "mqo_dev.cuh"):
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2605_06921_gb300", "csrc", f), "rb").read())
     if h.hexdigest() != m.group(1):
         return None
     return float(t.group(1))
+
+
+def step_kernel_traffic(workload, x_dtype, variant):
+    """DRAM bytes per launch of the step kernel variant (smem, smem_wide, global)."""
+    return profile_traffic(f"step_kernel_{workload}_{x_dtype}", variant, ("mqo_step.cu", "mqo_dev.cuh"))
 
 
 def gpu_arm(args):
@@ -492,9 +497,10 @@ def gpu_arm(args):
     return 0
 
 
-def fb_kernel_bytes(G, B):
-    """col + row_ptr read once, X read once, the gradient written once."""
-    return G.nnz * 4 + (G.n + 1) * 4 + 2 * G.n * B * 4
+def fb_kernel_bytes(G, B, writes_grad):
+    """col + row_ptr read once, X read once (forward), the gradient written
+    once (backward)."""
+    return G.nnz * 4 + (G.n + 1) * 4 + G.n * B * 4 + (G.n * B * 4 if writes_grad else 0)
 
 
 def oracle_autograd_sample(G, B, lam, target_s=12.0, cores=None):
@@ -599,13 +605,17 @@ def autograd_arm(args):
     # chunks, one more if some row is longer; the momentum step: one
     per_fb = 1 + int(G.degrees().max() > 512)
     launches_per_step = 2 * per_fb + 1
-    bwd_ms = ph["backward"] / args.steps
-    alg = fb_kernel_bytes(G, B)
+    # the forward launch (f_B per column: one SpMM pass, X read once); the
+    # backward is the same pass plus the gradient write and takes as long
+    fwd_ms = ph["forward"] / args.steps
+    alg = fb_kernel_bytes(G, B, False)
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg / (bwd_ms / 1e3) / 1e9
+    achieved = alg / (fwd_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "mqo::k_fb_units (f_B backward, fused SpMM gradient)",
-            "algorithmic_bytes_per_launch": alg, "backward_ms": bwd_ms,
+            "traffic": profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_units", ("mqo_grad.cu", "mqo_dev.cuh")),
+            "kernel": "mqo::k_fb_units (f_B forward; the fused SpMM backward is the same pass plus a write)",
+            "algorithmic_bytes_per_launch": alg, "forward_ms": fwd_ms,
+            "backward_hbm_gbs": fb_kernel_bytes(G, B, True) / (ph["backward"] / args.steps / 1e3) / 1e9,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     # end to end through the public API: X copied from pinned host memory
     # every step, forward + backward + optimiser step, the objective read back
