@@ -135,25 +135,32 @@ __device__ __forceinline__ void flush_step_counters(const StepArgs& a, unsigned 
 // ---------------------------------------------------------------- generic
 // The CTA first stages its item's row pointers and (up to kColCap) column
 // indices / weights in shared memory with coalesced loads, so that a row's
-// neighbour ids cost no dependent global load; each row then issues the
-// loads of its own x and V and of up to kGather neighbour rows of x before
-// consuming any of them.  A row group of LPR = B/VEC lanes owns one node.
+// neighbour ids cost no dependent global load.  A row group of LPR = B/VEC
+// lanes owns two rows at a time: it issues the loads of both rows' x and V
+// and of up to kGather neighbour rows of x for each before consuming any,
+// then runs both epilogues, so every lane keeps two rows' memory traffic in
+// flight.  MIS and WEIGHTED are compile-time: the unweighted MaxCut and MIS
+// variants carry no per-neighbour weight logic.
 constexpr int kColCap = 4096;  // staged column indices per item
-constexpr int kGather = 4;     // neighbour rows of x in flight per row group
+constexpr int kGather = 4;     // neighbour rows of x in flight per row and row group
+// rows a row group keeps in flight: two for narrow lanes, one for lanes of 4
+// or more trajectories (their packs and sums would not fit the registers of
+// two CTAs per SM)
+template <int VEC>
+__host__ __device__ constexpr int rows_in_flight() { return VEC >= 4 ? 1 : 2; }
 
-template <typename TX, typename TV, int VEC>
+template <typename TX, typename TV, int VEC, bool MIS, bool WEIGHTED>
 __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) {
   __shared__ unsigned long long s_cnt[3 * 128];
   __shared__ int32_t s_rp[kItemMaxNodes + 1];
   __shared__ int32_t s_col[kColCap];
-  __shared__ int8_t s_w[kColCap];
+  __shared__ int8_t s_w[WEIGHTED ? kColCap : 1];
   const int it = blockIdx.x;
   const Item item = a.g.items[it];
   const int g = item.g;
   const int64_t t = *a.tick;
   if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
   const int B = a.B;
-  const bool weighted = a.g.w != nullptr;
   const int32_t* __restrict__ rp = a.g.row_ptr;
   const int32_t* __restrict__ col = a.g.col;
   const int8_t* __restrict__ wts = a.g.w;
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) 
   const int32_t ncol = min(s_rp[nrows] - j0, kColCap);
   for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
     s_col[i] = __ldcs(col + j0 + i);
-    if (weighted) s_w[i] = wts[j0 + i];
+    if constexpr (WEIGHTED) s_w[i] = wts[j0 + i];
   }
   __syncthreads();
 
@@ -177,9 +184,8 @@ __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) 
   const int b0 = l * VEC;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const bool mis = a.problem == PROB_MIS;
-  const float thr = mis ? 0.5f : 0.0f;
-  const float lo = mis ? 0.0f : -1.0f;
+  const float thr = MIS ? 0.5f : 0.0f;
+  const float lo = MIS ? 0.0f : -1.0f;
   const TX* __restrict__ Xc = static_cast<const TX*>((t & 1) ? a.X1 : a.X0);
   TX* __restrict__ Xn = static_cast<TX*>((t & 1) ? a.X0 : a.X1);
   uint32_t* __restrict__ Zn = (t & 1) ? a.ZX0 : a.ZX1;
@@ -195,57 +201,97 @@ __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) 
 #pragma unroll
   for (int e = 0; e < VEC; ++e) c0[e] = c1[e] = c2[e] = 0;
 
-  for (int vr = warp * rpw + sub; vr < nrows; vr += nwarps * rpw) {
-    const int v = item.v0 + vr;
-    const int64_t base = (int64_t)v * B + b0;
-    const Pack<TX, VEC> xv = ld_pack<TX, VEC>(Xc + base);
-    const Pack<TV, VEC> vv = ld_pack_stream<TV, VEC>(V + base);
-    float acc[VEC];
-    int pos[VEC];
+  constexpr int ROWS = rows_in_flight<VEC>();
+  auto entry = [&](int32_t j, int32_t& u, int& w) {
+    const int32_t r = j - j0;
+    u = r < ncol ? s_col[r] : col[j];
+    if constexpr (WEIGHTED) w = (int)(r < ncol ? s_w[r] : wts[j]);
+    else w = 1;
+  };
+
+  // row group rows: vr (and vr + rpw when ROWS = 2), then ROWS*rpw*nwarps further
+  for (int vr = warp * rpw * ROWS + sub; vr < nrows; vr += nwarps * rpw * ROWS) {
+    const int vr2 = vr + rpw;
+    const bool two = ROWS == 2 && vr2 < nrows;
+    int v[ROWS], rs[ROWS], dg[ROWS];
+    v[0] = item.v0 + vr;
+    rs[0] = s_rp[vr];
+    dg[0] = s_rp[vr + 1] - rs[0];
+    if constexpr (ROWS == 2) {
+      v[1] = item.v0 + (two ? vr2 : vr);
+      rs[1] = two ? s_rp[vr2] : 0;
+      dg[1] = two ? s_rp[vr2 + 1] - s_rp[vr2] : 0;
+    }
+    Pack<TX, VEC> xv[ROWS];
+    Pack<TV, VEC> vv[ROWS];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
-    const int rs = s_rp[vr], re = s_rp[vr + 1];
-    int wsum = 0;
-    for (int j = rs; j < re; j += kGather) {
-      int u[kGather], w[kGather];
-      Pack<TX, VEC> p[kGather];
+    for (int r = 0; r < ROWS; ++r) {
+      const int64_t base = (int64_t)v[r] * B + b0;
+      xv[r] = ld_pack<TX, VEC>(Xc + base);
+      vv[r] = ld_pack_stream<TV, VEC>(V + base);
+    }
+    float acc[ROWS][VEC];
+    int pos[ROWS][VEC];
+    int wsum[ROWS];
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) {
-        const int jj = j + q;
-        const int r = jj - j0;
-        const bool in = jj < re;
-        u[q] = in ? (r < ncol ? s_col[r] : col[jj]) : v;  // past the row: a harmless load of v's own row
-        w[q] = in ? (weighted ? (int)(r < ncol ? s_w[r] : wts[jj]) : 1) : 0;
-      }
+    for (int r = 0; r < ROWS; ++r) {
+      wsum[r] = WEIGHTED ? 0 : dg[r];
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) p[q] = ld_pack<TX, VEC>(Xc + (int64_t)u[q] * B + b0);
+      for (int e = 0; e < VEC; ++e) { acc[r][e] = 0.0f; pos[r][e] = 0; }
+    }
+    int dmax = dg[0];
+    if constexpr (ROWS == 2) dmax = dg[0] > dg[1] ? dg[0] : dg[1];
+    for (int k = 0; k < dmax; k += kGather) {
+      int w[ROWS][kGather];
+      Pack<TX, VEC> p[ROWS][kGather];
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) {
-        if (j + q >= re) break;
-        wsum += w[q];
+      for (int r = 0; r < ROWS; ++r)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const float f = to_f(p[q].e[e]);
-          acc[e] = w[q] >= 0 ? acc[e] + f : acc[e] - f;
-          pos[e] += (f > thr) ? w[q] : 0;
+        for (int q = 0; q < kGather; ++q) {
+          int32_t u = v[r];  // past the row: a harmless load of the row's own x
+          w[r][q] = 0;
+          if (k + q < dg[r]) entry(rs[r] + k + q, u, w[r][q]);
+          p[r][q] = ld_pack<TX, VEC>(Xc + (int64_t)u * B + b0);
         }
-      }
-    }
-    Pack<TX, VEC> xo;
-    Pack<TV, VEC> vo;
-    unsigned zbits = 0u;
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-      bool zn;
-      step_element<TX, TV>(a, mis, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, (stepm >> e) & 1u, xo.e[e],
-                           vo.e[e], zn, c0[e], c1[e], c2[e]);
-      zbits |= (unsigned)zn << e;
+      for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int q = 0; q < kGather; ++q) {
+          if (k + q >= dg[r]) break;
+          if constexpr (WEIGHTED) wsum[r] += w[r][q];
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const float f = to_f(p[r][q].e[e]);
+            if constexpr (WEIGHTED) {
+              acc[r][e] = w[r][q] >= 0 ? acc[r][e] + f : acc[r][e] - f;
+              pos[r][e] += (f > thr) ? w[r][q] : 0;
+            } else {
+              acc[r][e] = acc[r][e] + f;
+              pos[r][e] += (f > thr);
+            }
+          }
+        }
     }
-    st_pack<TX, VEC>(Xn + base, xo);
-    st_pack<TV, VEC>(V + base, vo);
-    unsigned word = zbits << (b0 & 31);
-    for (int off = 1; off < K; off <<= 1) word |= __shfl_xor_sync(rmask, word, off);
-    if ((l % K) == 0) Zn[(int64_t)v * a.Bw + (b0 >> 5)] = word;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      if (r == 1 && !two) break;
+      Pack<TX, VEC> xo;
+      Pack<TV, VEC> vo;
+      unsigned zbits = 0u;
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        bool zn;
+        step_element<TX, TV>(a, MIS, thr, lo, xv[r].e[e], vv[r].e[e], acc[r][e], pos[r][e], wsum[r],
+                             (stepm >> e) & 1u, xo.e[e], vo.e[e], zn, c0[e], c1[e], c2[e]);
+        zbits |= (unsigned)zn << e;
+      }
+      const int64_t base = (int64_t)v[r] * B + b0;
+      st_pack<TX, VEC>(Xn + base, xo);
+      st_pack<TV, VEC>(V + base, vo);
+      unsigned word = zbits << (b0 & 31);
+      for (int off = 1; off < K; off <<= 1) word |= __shfl_xor_sync(rmask, word, off);
+      if ((l % K) == 0) Zn[(int64_t)v[r] * a.Bw + (b0 >> 5)] = word;
+    }
   }
   flush_step_counters<VEC>(a, s_cnt, g, it, b0, lpr, c0, c1, c2, stepm);
 }
@@ -560,7 +606,9 @@ bool step_wide_possible(int B, int x_dtype) { return x_dtype != DT_F32 ? (B == 3
 
 template <typename TX, typename TV, int VEC>
 static cudaError_t launch_vec(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step_g<TX, TV, VEC><<<grid, 512, 0, s>>>(a);
+  if (a.problem == PROB_MIS) k_step_g<TX, TV, VEC, true, false><<<grid, 512, 0, s>>>(a);
+  else if (a.g.w) k_step_g<TX, TV, VEC, false, true><<<grid, 512, 0, s>>>(a);
+  else k_step_g<TX, TV, VEC, false, false><<<grid, 512, 0, s>>>(a);
   return cudaGetLastError();
 }
 
