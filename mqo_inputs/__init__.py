@@ -251,6 +251,12 @@ def workload_mis_batched(num_graphs: int = 512, first_seed: int = 0):
     return pack(gs)
 
 
+def workload_er_table(n: int = 1000, d: float = 100.0, num_graphs: int = 8, first_seed: int = 0):
+    """num_graphs ER graphs G(n, p = d/n) (the (n, d) parameterisation of the
+    paper's ER experiments), seeds first_seed.., packed."""
+    return pack([erdos_renyi(n, d / n, first_seed + k) for k in range(num_graphs)])
+
+
 def workload_maxcut_regular(n: int = 100_000, signed: bool = False, seed: int = 0):
     """Random 3-regular graph (optionally with uniform ±1 edge weights)."""
     return random_regular(n, 3, seed, signed_weights=signed)

@@ -586,12 +586,16 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     s->step_smem = generic ? 0 : s->step_smem_max;
     // MQO_STEP_KERNEL=wide: the shared-memory kernel with 16-byte lanes
     s->S.step_wide = force && strcmp(force, "wide") == 0 && step_wide_possible(B, p->x_dtype) ? 1 : 0;
-    // MQO_DISC_KERNEL=pairs selects the three node-parallel discrete passes
-    // even when every member graph's bit words fit in shared memory
+    // The fused per-graph discrete kernel runs one CTA per member graph, so
+    // it is the default only with at least half as many member graphs as
+    // SMs; with fewer, the node-parallel passes (several CTAs per item) fill
+    // the GPU.  MQO_DISC_KERNEL=pairs | graph forces either when possible.
     const char* dforce = getenv("MQO_DISC_KERNEL");
     const bool pairs = dforce && strcmp(dforce, "pairs") == 0;
+    const bool fused = dforce && strcmp(dforce, "graph") == 0;
     const size_t dneed = disc_graph_smem_bytes(B, max_ng);
-    s->disc_smem_max = (B >= 32 && dneed <= kDiscSmemLimit) ? dneed : 0;
+    const bool few = 2 * g->G < g->sms;
+    s->disc_smem_max = (B >= 32 && dneed <= kDiscSmemLimit && (!few || fused)) ? dneed : 0;
     s->disc_smem = pairs ? 0 : s->disc_smem_max;
   }
   const size_t TR = (size_t)T * S.R;
@@ -617,6 +621,12 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
   if ((st = dalloc(&s->d_pending, 1, &s->allocs)) != MQO_OK) return bail(st);
   if (cudaMallocHost(&s->h_pending, sizeof(int32_t)) != cudaSuccess) return bail(fail(MQO_ENOMEM, "pinned alloc"));
   s->grid = std::max(1, std::min(g->num_items, g->sms * 8));
+  {
+    // node-parallel kernels take several CTAs per item when there are few
+    // items, so that about four CTAs' worth of nodes reach every SM
+    const int target = g->sms * 4;
+    S.split = g->num_items >= target ? 1 : std::min(8, (target + g->num_items - 1) / g->num_items);
+  }
   {
     cudaEventRecord(s->ev_in, s->user);
     cudaStreamWaitEvent(s->work, s->ev_in, 0);

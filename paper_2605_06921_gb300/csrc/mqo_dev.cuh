@@ -115,6 +115,7 @@ struct SolverDev {
   int32_t R;        // counter replicas per trajectory (item i adds into replica i % R)
   int32_t step_vec; // trajectories per lane of the global-memory step kernel (0: B/32 or 1)
   int32_t step_wide; // shared-memory step kernel with 16-byte lanes
+  int32_t split;    // CTAs per item of the node-parallel kernels (several when there are few items)
   void* X0;         // relaxed x: tick t reads X[t&1] and writes X[(t+1)&1]
   void* X1;
   void* V;          // momentum
@@ -145,6 +146,20 @@ struct SolverDev {
   int64_t* pval;    // [G*K] values of the pool members, best first
   int32_t* pbase;   // [G*B] pool slot a trajectory resets / searches from (-1: the empty set)
 };
+
+// The item of this CTA and its slice of the item's nodes when each item is
+// split over S.split CTAs (CTA c takes slice c % split); false if the slice
+// is empty.
+__device__ __forceinline__ bool item_slice(const SolverDev& S, int& it, Item& item) {
+  it = blockIdx.x / S.split;
+  item = S.g.items[it];
+  const int part = blockIdx.x - it * S.split;
+  const int per = (item.v1 - item.v0 + S.split - 1) / S.split;
+  const int r0 = item.v0 + part * per;
+  item.v1 = item.v1 < r0 + per ? item.v1 : r0 + per;
+  item.v0 = r0;
+  return item.v0 < item.v1;
+}
 
 // sum of the R replicas of a trajectory's counters
 __device__ __forceinline__ Counters sum_replicas(const Counters* c, int64_t tau, int R) {

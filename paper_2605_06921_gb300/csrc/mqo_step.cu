@@ -37,6 +37,7 @@ namespace mqo {
 struct StepArgs {
   GraphDev g;
   int32_t B, Bw, R, problem, objective;
+  int32_t split;  // generic kernel: CTAs per item, each taking a contiguous slice of its rows
   float alpha, momentum, gamma, lambda_;
   void* X0;
   void* X1;
@@ -155,11 +156,19 @@ __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) 
   __shared__ int32_t s_rp[kItemMaxNodes + 1];
   __shared__ int32_t s_col[kColCap];
   __shared__ int8_t s_w[WEIGHTED ? kColCap : 1];
-  const int it = blockIdx.x;
-  const Item item = a.g.items[it];
+  const int it = blockIdx.x / a.split;
+  Item item = a.g.items[it];
   const int g = item.g;
   const int64_t t = *a.tick;
   if (a.gflag_step && a.gflag_step[g] != (int32_t)(t + 1)) return;
+  {  // this CTA's slice of the item's rows
+    const int part = blockIdx.x - it * a.split;
+    const int per = (item.v1 - item.v0 + a.split - 1) / a.split;
+    const int r0 = item.v0 + part * per;
+    item.v1 = min(item.v1, r0 + per);
+    item.v0 = r0;
+    if (item.v0 >= item.v1) return;
+  }
   const int B = a.B;
   const int32_t* __restrict__ rp = a.g.row_ptr;
   const int32_t* __restrict__ col = a.g.col;
@@ -646,6 +655,7 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   a.ZX0 = S.ZX0;
   a.ZX1 = S.ZX1;
   a.cnt = cnt;
+  a.split = 1;
   a.act = act;
   a.gflag_step = gflag_step;
   a.tick = S.tick;
@@ -653,7 +663,11 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   const bool sp = smem > 0;
   const bool wide = S.step_wide != 0;
   const bool mis = S.p.problem == PROB_MIS;
-  const int grid = S.g.num_items;
+  int grid = S.g.num_items;
+  if (!sp) {  // few items (a handful of member graphs): several CTAs per item
+    a.split = S.split;
+    grid = S.g.num_items * a.split;
+  }
   const int xd = S.p.x_dtype, vd = S.p.v_dtype;
   if (xd == DT_F32) return launch_tv<float, float>(vec, sp, wide, smem, mis, a, grid, stream);
   if (xd == DT_BF16 && vd == DT_BF16) return launch_tv<__nv_bfloat16, __nv_bfloat16>(vec, sp, wide, smem, mis, a, grid, stream);

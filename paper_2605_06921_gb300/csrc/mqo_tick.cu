@@ -431,10 +431,11 @@ __device__ __forceinline__ void set_bit_atomic(uint32_t* words, int64_t v, int B
 __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
   __shared__ int s_list[128];
   __shared__ int s_n;
-  const int it = blockIdx.x;
   const int64_t t = *S.tick;
   if (S.any[0] != (int32_t)(t + 1)) return;
-  const Item item = S.g.items[it];
+  int it;
+  Item item;
+  if (!item_slice(S, it, item)) return;
   if (S.gflag[item.g] != (int32_t)(t + 1)) return;
   const int B = S.B, Bw = S.Bw;
   const int g = item.g;
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
 }
 
 cudaError_t launch_apply(const SolverDev& S, cudaStream_t stream) {
-  k_apply<<<S.g.num_items, kPairThreads, 0, stream>>>(S);
+  k_apply<<<S.g.num_items * S.split, kPairThreads, 0, stream>>>(S);
   return cudaGetLastError();
 }
 
@@ -551,10 +552,11 @@ __device__ __forceinline__ void flush_pair_counters(const SolverDev& S, unsigned
 // pass 0 = A (decide / propose), 1 = B (commit), 2 = C (count)
 __global__ void __launch_bounds__(kPairThreads) k_disc(SolverDev S, int pass) {
   __shared__ unsigned long long s_cnt[4 * 128];
-  const int it = blockIdx.x;
   const int64_t t = *S.tick;
   if (S.any[1] != (int32_t)(t + 1)) return;
-  const Item item = S.g.items[it];
+  int it;
+  Item item;
+  if (!item_slice(S, it, item)) return;
   const int G = S.g.num_graphs;
   if (S.gflag[G + item.g] != (int32_t)(t + 1)) return;
   const int B = S.B, Bw = S.Bw;
@@ -735,7 +737,7 @@ __global__ void __launch_bounds__(kPairThreads) k_disc(SolverDev S, int pass) {
 }
 
 cudaError_t launch_disc(const SolverDev& S, int pass, cudaStream_t stream) {
-  k_disc<<<S.g.num_items, kPairThreads, 0, stream>>>(S, pass);
+  k_disc<<<S.g.num_items * S.split, kPairThreads, 0, stream>>>(S, pass);
   return cudaGetLastError();
 }
 

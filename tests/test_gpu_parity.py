@@ -258,16 +258,22 @@ def test_machine_config1_2000_ticks(mq):
     assert oracle.eval_mis(og, trs[0][0].zbest)[1:] == (0, 0, 0)
 
 
+@pytest.mark.parametrize("disc", ["graph", "pairs"])
 @pytest.mark.parametrize("B", [1, 8, 32])
-def test_machine_packed_mis(mq, B):
+def test_machine_packed_mis(mq, monkeypatch, B, disc):
+    """both discrete-kernel plans: the fused per-graph kernel (forced here; by
+    default it serves batches of many member graphs) and the node-parallel
+    passes"""
+    monkeypatch.setenv("MQO_DISC_KERNEL", disc)
     G = small_batch(4, 30, 70, 0.15, seed=B)
     p = mq.params(batch=B, alpha=0.8, momentum=0.45, rho=0.6, t_gs=4, descent_cap=25, seed=B)
     _machine(mq, G, p, 400, trace=30)
 
 
 @pytest.mark.parametrize("problem", [0, 1])
-def test_autotune_keeps_results(mq, problem):
+def test_autotune_keeps_results(mq, monkeypatch, problem):
     """Autotuning mid-run (every plan tried, state restored) changes no tick of the machine."""
+    monkeypatch.setenv("MQO_DISC_KERNEL", "graph")  # make the fused discrete plan one of the candidates
     G = small_batch(4, 60, 120, 0.1, seed=11)
     if problem == 0:
         p = mq.params(batch=32, alpha=0.8, momentum=0.45, rho=0.6, t_gs=4, descent_cap=25, seed=3)
@@ -283,8 +289,10 @@ def test_machine_mis_low_precision(mq):
     _machine(mq, G, p, 300)
 
 
+@pytest.mark.parametrize("disc", ["graph", "pairs"])
 @pytest.mark.parametrize("weighted", [False, True])
-def test_machine_maxcut(mq, weighted):
+def test_machine_maxcut(mq, monkeypatch, weighted, disc):
+    monkeypatch.setenv("MQO_DISC_KERNEL", disc)
     G = mi.pack([mi.random_regular(80, 3, 5), mi.erdos_renyi(60, 0.1, 6)])
     if weighted:
         G = signed(G, 7)

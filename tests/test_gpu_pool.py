@@ -86,7 +86,8 @@ def cut_params(mq, B, K, **kw):
 
 
 @pytest.mark.parametrize("B,K", [(4, 1), (8, 3), (32, 8), (16, 40)])
-def test_pool_mis(mq, B, K):
+def test_pool_mis(mq, monkeypatch, B, K):
+    monkeypatch.setenv("MQO_DISC_KERNEL", "graph" if B >= 32 else "pairs")
     G = small_batch(3, 30, 70, 0.15, seed=K)
     _pool_machine(mq, G, mis_params(mq, B, K, seed=B + K), [120, 300, 500], trace=20)
 
