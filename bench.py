@@ -506,6 +506,15 @@ def gpu_arm(args):
             per_graph = vals.reshape(G.num_graphs, B).max(axis=1)
             quality[label] = {"best_per_graph_mean": float(per_graph.mean()), "best_per_graph": per_graph.tolist(),
                               "seconds": dt}
+            # gains breakdown of each graph's best trajectory (first descent,
+            # then the increases from resets / restarts and from local search)
+            sts = s.traj_state()
+            pick = vals.reshape(G.num_graphs, B).argmax(axis=1)
+            br = [sts[gi * B + int(pick[gi])] for gi in range(G.num_graphs)]
+            quality[label]["breakdown_mean"] = {
+                "first_descent": float(np.mean([x["first_value"] for x in br])),
+                "gain_resets": float(np.mean([x["gain_descent"] for x in br])),
+                "gain_local_search": float(np.mean([x["gain_ls"] for x in br]))}
             s.close()
             g.close()
 

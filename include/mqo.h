@@ -123,6 +123,12 @@ typedef struct {
   int64_t descents;     /* finished descents */
   int64_t held;         /* pool mode: value of the set held while waiting, INT64_MIN if none
                            (or a capped, unrepaired MIS point, which is no candidate) */
+  /* gains breakdown (the paper's appendix on where mQO's gains come from):
+   * best = first_value + gain_descent + gain_ls once a set was accepted */
+  int64_t first_value;  /* first accepted value (end of the first descent), INT64_MIN if none */
+  int64_t gain_descent; /* sum of the strict improvements accepted from later descents
+                           (global-reset rounds and restarts; pool merges in pool mode) */
+  int64_t gain_ls;      /* sum of the strict improvements accepted from local search */
 } mqo_traj_info;
 
 /* ---------------------------------------------------------------- graphs */

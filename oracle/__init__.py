@@ -72,6 +72,7 @@ class OrcState(C.Structure):
         ("best", C.c_int64), ("ticks", C.c_int64), ("last_round", C.c_int32), ("last_commits", C.c_int64),
         ("ev_value", C.c_int64), ("ev_a", C.c_int64), ("ev_b", C.c_int64),
         ("accepts", C.c_int64), ("descents", C.c_int64), ("held", C.c_int64),
+        ("first_value", C.c_int64), ("gain_descent", C.c_int64), ("gain_ls", C.c_int64),
     ]
 
     def as_dict(self):

@@ -93,6 +93,13 @@ typedef struct {
   int64_t accepts;
   int64_t descents;
   int64_t held;       /* pool mode: value of the set held while waiting, INT64_MIN if none */
+  /* where the best value came from (the gains breakdown of the appendix on
+   * mQO's gains): the first accepted value (the end of the first descent's
+   * gradient updates), then the strict improvements accepted from later
+   * descents (global resets and restarts) and from local search */
+  int64_t first_value; /* INT64_MIN until the first acceptance */
+  int64_t gain_descent;
+  int64_t gain_ls;
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -695,9 +702,17 @@ typedef struct {
   orc_state* st;
 } orc_traj;
 
-static void accept(orc_traj* T, const uint8_t* src, int64_t value) {
+/* book a strict improvement of the best value by its source */
+static void credit(orc_state* st, int64_t value, int from_ls) {
+  if (st->best == INT64_MIN) st->first_value = value;
+  else if (from_ls) st->gain_ls += value - st->best;
+  else st->gain_descent += value - st->best;
+}
+
+static void accept(orc_traj* T, const uint8_t* src, int64_t value, int from_ls) {
   orc_state* st = T->st;
   if (value > st->best) {
+    credit(st, value, from_ls);
     st->best = value;
     memcpy(T->zbest, src, (size_t)T->g->n);
     st->accepts += 1;
@@ -777,7 +792,7 @@ static void tick(orc_traj* T) {
       int pass = mis ? (st->ev_a == 0 && st->ev_b == 0) : (st->ev_a == 0);
       if (pass) {
         st->descents += 1;
-        accept(T, T->zx_prev, st->ev_value);
+        accept(T, T->zx_prev, st->ev_value, 0);
         round = after_accept(T);
       } else if (st->s >= p->descent_cap) {
         st->descents += 1;
@@ -790,7 +805,7 @@ static void tick(orc_traj* T) {
             round = after_accept(T);
           }
         } else {
-          accept(T, T->zx_prev, st->ev_value);
+          accept(T, T->zx_prev, st->ev_value, 0);
           round = after_accept(T);
         }
       }
@@ -799,7 +814,7 @@ static void tick(orc_traj* T) {
     if (st->ev_a > 0) round = ORC_R_DROP;
     else if (st->ev_b > 0) round = ORC_R_COMPLETE;
     else {
-      accept(T, T->zwork, st->ev_value);
+      accept(T, T->zwork, st->ev_value, 0);
       round = after_accept(T);
     }
   } else { /* local search */
@@ -814,7 +829,7 @@ static void tick(orc_traj* T) {
       else done = 1;
     }
     if (done) {
-      accept(T, T->zwork, st->ev_value);
+      accept(T, T->zwork, st->ev_value, 1);
       start_outer(T);
       round = ORC_R_NONE;
     }
@@ -846,6 +861,7 @@ ORC_API void orc_state_init(orc_state* st) {
   st->best = INT64_MIN;
   st->last_round = ORC_R_NONE;
   st->held = INT64_MIN;
+  st->first_value = INT64_MIN;
 }
 
 /* Run one trajectory for `nticks` ticks from a fresh start (outer
@@ -1002,10 +1018,11 @@ static void tick_pool(orc_traj* T, int dec, const uint8_t* base, int ls_me) {
   st->ticks += 1;
 }
 
-static void set_best_all(orc_traj* T, int B, orc_pool* P, int64_t value, const uint8_t* bits) {
+static void set_best_all(orc_traj* T, int B, orc_pool* P, int64_t value, const uint8_t* bits, int from_ls) {
   P->best = value;
   for (int b = 0; b < B; ++b) {
     if (T[b].zbest != bits) memcpy(T[b].zbest, bits, (size_t)T[b].g->n);
+    credit(T[b].st, value, from_ls);
     T[b].st->best = value;
     T[b].st->accepts += 1;
   }
@@ -1031,7 +1048,7 @@ static int pool_control(orc_traj* T, int B, orc_pool* P, uint8_t* pool_bits, int
       if (T[b].st->held != INT64_MIN && T[b].st->held > bv) { bv = T[b].st->held; win = b; }
     if (win >= 0) {
       memcpy(tmp, T[win].zwork, (size_t)n);
-      set_best_all(T, B, P, bv, tmp);
+      set_best_all(T, B, P, bv, tmp, 1);
     }
     P->epoch = ORC_EP_DESCENT;
     return ORC_DEC_OUTER;
@@ -1063,7 +1080,7 @@ static int pool_control(orc_traj* T, int B, orc_pool* P, uint8_t* pool_bits, int
   P->merges += 1;
   free(newbits); free(cv); free(cs);
   /* steps 5 / 12 */
-  if (P->count > 0 && pool_vals[0] > P->best) set_best_all(T, B, P, pool_vals[0], pool_bits);
+  if (P->count > 0 && pool_vals[0] > P->best) set_best_all(T, B, P, pool_vals[0], pool_bits, 0);
   const orc_state* s0 = T[0].st;
   if (s0->r < p->t_gs) {
     for (int b = 0; b < B; ++b) {

@@ -50,6 +50,7 @@ class TrajInfo(C.Structure):
         ("best", C.c_int64), ("ticks", C.c_int64), ("last_round", C.c_int32), ("pad0", C.c_int32),
         ("last_commits", C.c_int64), ("ev_value", C.c_int64), ("ev_a", C.c_int64), ("ev_b", C.c_int64),
         ("accepts", C.c_int64), ("descents", C.c_int64), ("held", C.c_int64),
+        ("first_value", C.c_int64), ("gain_descent", C.c_int64), ("gain_ls", C.c_int64),
     ]
 
     def as_dict(self):

@@ -892,7 +892,7 @@ mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_byt
                            int32_t* replicas) {
   if (!s) return fail(MQO_EINVAL, "null solver");
   const int B = s->S.B;
-  const int vec = s->step_smem > 0 ? 0 : (s->S.step_vec > 0 ? s->S.step_vec : (B >= 32 ? B / 32 : 1));
+  const int vec = s->step_smem > 0 ? 0 : (s->S.step_vec > 0 ? s->S.step_vec : default_step_vec(B, s->S.p.x_dtype));
   if (step_kernel)
     *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0) |
                    (s->step_smem > 0 && s->S.step_wide ? 4 : 0) | (vec << 4);
@@ -973,6 +973,9 @@ mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
     o.accepts = t.accepts;
     o.descents = t.descents;
     o.held = t.held;
+    o.first_value = t.first_value;
+    o.gain_descent = t.gain_descent;
+    o.gain_ls = t.gain_ls;
   }
   return MQO_OK;
 }

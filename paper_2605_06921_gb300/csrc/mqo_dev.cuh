@@ -69,7 +69,18 @@ struct __align__(16) TrajState {
   uint32_t rkeys[6];
   int64_t rk;
   int64_t held;  // pool mode: value of the held set (INT64_MIN: none, or not a candidate)
+  // gains breakdown: the first accepted value (end of the first descent's
+  // gradient updates), then the strict improvements accepted from later
+  // descents (global resets, restarts) and from local search
+  int64_t first_value, gain_descent, gain_ls;
 };
+
+// book a strict improvement of st.best to `value` by its source
+__device__ __forceinline__ void credit_gain(TrajState& st, int64_t value, bool from_ls) {
+  if (st.best == (int64_t)(-9223372036854775807LL - 1)) st.first_value = value;
+  else if (from_ls) st.gain_ls += value - st.best;
+  else st.gain_descent += value - st.best;
+}
 
 // Per member graph state of the pool machine (pmQO, Alg. 3/4).
 struct PoolState {

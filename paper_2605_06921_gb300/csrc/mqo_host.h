@@ -15,6 +15,7 @@ enum CtrlMode : int { CTRL_MACHINE = 0, CTRL_LS_BEGIN = 1, CTRL_LS = 2, CTRL_RES
 cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, const int32_t* gflag_step,
                         size_t smem, cudaStream_t stream);
 bool step_wide_possible(int B, int x_dtype);
+int default_step_vec(int B, int x_dtype);
 size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng);
 
 cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream);

@@ -611,6 +611,18 @@ static cudaError_t launch_smem(int B, bool wide, size_t smem, bool mis, const St
   return cudaErrorInvalidValue;
 }
 
+// Default trajectories per lane of the global-memory step kernel (before
+// any autotuning): at least 8 bytes of x per lane where the batch allows it,
+// and at most 32 lanes per row.
+int default_step_vec(int B, int x_dtype) {
+  const int sx = x_dtype == DT_F32 ? 4 : 2;
+  int vec = 8 / sx;
+  if (vec < B / 32) vec = B / 32;
+  if (vec > B) vec = B;
+  if (vec > 4) vec = 4;
+  return vec;
+}
+
 bool step_wide_possible(int B, int x_dtype) { return x_dtype != DT_F32 ? (B == 32 || B == 64 || B == 128) : (B == 32 || B == 64); }
 
 template <typename TX, typename TV, int VEC>
@@ -659,7 +671,7 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   a.act = act;
   a.gflag_step = gflag_step;
   a.tick = S.tick;
-  const int vec = S.step_vec > 0 ? S.step_vec : (S.B >= 32 ? S.B / 32 : 1);
+  const int vec = S.step_vec > 0 ? S.step_vec : default_step_vec(S.B, S.p.x_dtype);
   const bool sp = smem > 0;
   const bool wide = S.step_wide != 0;
   const bool mis = S.p.problem == PROB_MIS;

@@ -49,8 +49,9 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
   int act = 0;
   int round = RD_NONE;
 
-  auto accept = [&](int bit, int64_t value) {
+  auto accept = [&](int bit, int64_t value, bool from_ls) {
     if (value > st.best) {
+      credit_gain(st, value, from_ls);
       st.best = value;
       act |= bit;
       st.accepts += 1;
@@ -109,7 +110,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
         else done = true;
       }
       if (done) {
-        accept(ACT_ACC_WORK, st.ev_value);
+        accept(ACT_ACC_WORK, st.ev_value, true);
         st.ls_done = 1;
         round = RD_NONE;
       }
@@ -121,6 +122,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
     const PoolState ps = S.pool[g];
     const int b = (int)(tau - (int64_t)g * S.B);
     if (ps.best_src >= 0) {  // the graph's best set was replaced (steps 5, 12, 13)
+      credit_gain(st, ps.best, ps.best_src >= S.K);
       st.best = ps.best;
       st.accepts += 1;
     }
@@ -229,7 +231,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
         const bool pass = mis ? (st.ev_a == 0 && st.ev_b == 0) : (st.ev_a == 0);
         if (pass) {
           st.descents += 1;
-          accept(ACT_ACC_ZX, st.ev_value);
+          accept(ACT_ACC_ZX, st.ev_value, false);
           round = after_accept();
         } else if (st.s >= p.cap) {
           st.descents += 1;
@@ -242,7 +244,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
               round = after_accept();
             }
           } else {
-            accept(ACT_ACC_ZX, st.ev_value);
+            accept(ACT_ACC_ZX, st.ev_value, false);
             round = after_accept();
           }
         }
@@ -251,7 +253,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
       if (st.ev_a > 0) round = RD_DROP;
       else if (st.ev_b > 0) round = RD_COMPLETE;
       else {
-        accept(ACT_ACC_WORK, st.ev_value);
+        accept(ACT_ACC_WORK, st.ev_value, false);
         round = after_accept();
       }
     } else if (st.phase == PH_LS) {
@@ -266,7 +268,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
         else done = true;
       }
       if (done) {
-        accept(ACT_ACC_WORK, st.ev_value);
+        accept(ACT_ACC_WORK, st.ev_value, true);
         start_outer();
         round = RD_NONE;
       }
@@ -428,9 +430,20 @@ __device__ __forceinline__ void set_bit_atomic(uint32_t* words, int64_t v, int B
   else atomicAnd(wp, ~bit);
 }
 
+// Each CTA (a slice of one item) first lists, in increasing order, the
+// trajectories of its member graph that have an apply action this tick and
+// caches their actions, reset keys and bases in shared memory; it then visits
+// only those (node, trajectory) pairs, trajectory fastest, so that the x and V
+// writes of one node's listed trajectories are adjacent.  Bit updates are
+// atomic (several listed trajectories share a node's word).
 __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
   __shared__ int s_list[128];
-  __shared__ int s_n;
+  __shared__ int s_act[128];
+  __shared__ uint32_t s_keys[128][6];
+  __shared__ int64_t s_rk[128];
+  __shared__ int32_t s_o[128];
+  __shared__ int32_t s_pb[128];
+  __shared__ int s_wcnt[4];
   const int64_t t = *S.tick;
   if (S.any[0] != (int32_t)(t + 1)) return;
   int it;
@@ -439,12 +452,31 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
   if (S.gflag[item.g] != (int32_t)(t + 1)) return;
   const int B = S.B, Bw = S.Bw;
   const int g = item.g;
-  if (threadIdx.x == 0) s_n = 0;
+  // ordered compaction of the acting trajectories (B <= 128: warps 0..3)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int myact = 0;
+  if (threadIdx.x < B) myact = S.act[(int64_t)g * B + threadIdx.x];
+  const bool on = threadIdx.x < B && (myact & ACT_APPLY_MASK);
+  const unsigned bal = __ballot_sync(0xffffffffu, on);
+  if (warp < 4 && lane == 0) s_wcnt[warp] = __popc(bal);
   __syncthreads();
-  for (int b = threadIdx.x; b < B; b += blockDim.x)
-    if (S.act[(int64_t)g * B + b] & ACT_APPLY_MASK) s_list[atomicAdd(&s_n, 1)] = b;
+  if (on) {
+    int pos = __popc(bal & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
+    const int64_t tau = (int64_t)g * B + threadIdx.x;
+    s_list[pos] = threadIdx.x;
+    s_act[pos] = myact;
+    if (myact & ACT_RESET) {
+      const TrajState& st = S.st[tau];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) s_keys[pos][i] = st.rkeys[i];
+      s_rk[pos] = st.rk;
+    }
+    if (myact & ACT_INIT) s_o[pos] = S.st[tau].o;
+    s_pb[pos] = (myact & ACT_POOL) ? S.pbase[tau] : -1;
+  }
   __syncthreads();
-  const int nact = s_n;
+  const int nact = s_wcnt[0] + s_wcnt[1] + s_wcnt[2] + s_wcnt[3];
   const int nodes = item.v1 - item.v0;
   const bool mis = S.p.problem == PROB_MIS;
   const float thr = mis ? 0.5f : 0.0f;
@@ -454,10 +486,11 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
   const int32_t off = S.g.node_off[g];
   const uint32_t n_g = (uint32_t)(S.g.node_off[g + 1] - off);
   for (int idx = threadIdx.x; idx < nact * nodes; idx += blockDim.x) {
-    const int b = s_list[idx / nodes];
-    const int64_t v = item.v0 + idx % nodes;
+    const int j = idx % nact;
+    const int b = s_list[j];
+    const int64_t v = item.v0 + idx / nact;
     const int64_t tau = (int64_t)g * B + b;
-    const int act = S.act[tau];
+    const int act = s_act[j];
     bool zb = get_bit(S.Zbest, v, Bw, b);
     if (act & (ACT_ACC_ZX | ACT_ACC_WORK)) {
       const bool src = (act & ACT_ACC_ZX) ? get_bit(Zp, v, Bw, b) : get_bit(S.Zwork, v, Bw, b);
@@ -467,7 +500,7 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
     // pool mode: the base of a reset / local search is pool member pbase[tau]
     bool base = zb;
     if (act & ACT_POOL) {
-      const int32_t k = S.pbase[tau];
+      const int32_t k = s_pb[j];
       base = k >= 0 && ((S.Pool[v * S.Kw + (k >> 5)] >> (k & 31)) & 1u);
     }
     if (act & (ACT_WORK_ZX | ACT_WORK_BEST)) {
@@ -478,16 +511,11 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
       const uint32_t vl = (uint32_t)(v - off);
       float x;
       if (act & ACT_RESET) {
-        const TrajState& st = S.st[tau];
         x = base ? 1.0f : (mis ? 0.0f : -1.0f);
-        uint32_t keys[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) keys[i] = st.rkeys[i];
-        if ((int64_t)feistel_sigma(n_g, keys, vl) < st.rk) x = 0.0f;
+        if ((int64_t)feistel_sigma(n_g, s_keys[j], vl) < s_rk[j]) x = 0.0f;
       } else {
         const Params& p = S.p;
-        const int32_t o = S.st[tau].o;
-        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)o, (uint64_t)vl, 0ULL, p.seed, (uint64_t)tau);
+        const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)s_o[j], (uint64_t)vl, 0ULL, p.seed, (uint64_t)tau);
         const float lo = mis ? 0.0f : -1.0f, hi = 1.0f;
         if (p.init_kind == 0) {
           const float u = unit24(r.v[0]);
@@ -901,6 +929,9 @@ __global__ void k_ls_merge(TrajState* st, const TrajState* saved, int64_t* bestv
   TrajState s = saved[i];
   s.best = st[i].best;
   s.accepts = st[i].accepts;
+  s.first_value = st[i].first_value;
+  s.gain_descent = st[i].gain_descent;
+  s.gain_ls = st[i].gain_ls;
   st[i] = s;
   bestv[i] = s.best;
 }
@@ -935,6 +966,8 @@ __global__ void k_state_init(SolverDev S) {
     for (int i = 0; i < 6; ++i) st.rkeys[i] = 0u;
     st.rk = 0;
     st.held = (int64_t)(-9223372036854775807LL - 1);
+    st.first_value = st.held;
+    st.gain_descent = st.gain_ls = 0;
     S.st[tau] = st;
     if (S.K > 0 && tau < S.g.num_graphs) {
       PoolState ps;

@@ -242,7 +242,7 @@ def _machine(mq, G, p, nticks, trace=0, tune_at=None):
             want = tr.state
             got = states[t]
             for key in ("phase", "s", "r", "o", "best", "ticks", "last_round", "last_commits", "ev_value", "ev_a",
-                        "ev_b", "accepts", "descents"):
+                        "ev_b", "accepts", "descents", "first_value", "gain_descent", "gain_ls"):
                 assert got[key] == want[key], (g, b, key, got[key], want[key])
             assert vals[t] == want["best"]
             assert np.array_equal(z[lo:hi, b], tr.zbest), (g, b)
