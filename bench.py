@@ -357,6 +357,7 @@ def gpu_arm(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     info_launches = [0]
+    objective_probe = {}
 
     def measure(x_dtype, v_dtype, steps, warmup, sample_clocks, autotune=False):
         g = mq.Graph(G)
@@ -385,6 +386,28 @@ def gpu_arm(args):
         info = s.info()
         if tuned:
             info["autotune_ms_per_tick"] = tuned["ms_per_tick"]
+        if sample_clocks:
+            # the FP64 relaxed objective of the final iterate (timed on the
+            # device) and, for a few sampled trajectories, the stored x, so
+            # that the cpu_baseline leg can state its error against the oracle
+            o0 = torch.cuda.Event(enable_timing=True)
+            o1 = torch.cuda.Event(enable_timing=True)
+            o0.record()
+            obj = s.objective_f64()
+            o1.record()
+            torch.cuda.synchronize()
+            x = s.get_x()
+            st = s.traj_state()
+            objective_probe["ms"] = o0.elapsed_time(o1)
+            objective_probe["samples"] = []
+            for t in range(0, G.num_graphs * B, max(1, (G.num_graphs * B) // 8)):
+                gi, b = divmod(t, B)
+                if st[t]["phase"] != 0:  # x is defined in a descent only
+                    continue
+                lo, hi = int(G.node_offsets[gi]) if G.node_offsets is not None else 0, \
+                    int(G.node_offsets[gi + 1]) if G.node_offsets is not None else G.n
+                objective_probe["samples"].append((gi, t, x[lo:hi, b].float().cpu().numpy().astype(np.float64),
+                                                   float(obj[t].item())))
         s.close()
         g.close()
         return ms, phase_ms, clocks, vals, info
@@ -519,8 +542,22 @@ def gpu_arm(args):
             g.close()
 
     cpu = None
+    objective_f64 = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(G, wl, xd, vd, target_s=12.0, pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
+        # error of the device's FP64 relaxed objective ((Ax)_v accumulated in
+        # float32) against the oracle's all-double objective of the same x
+        import oracle
+        errs = []
+        for gi, t, xs, got in objective_probe.get("samples", []):
+            og = oracle.Graph(G.subgraph(gi) if G.num_graphs > 1 else G)
+            if wl["problem"] == 0:
+                want = oracle.objective_f64(og, 0, wl.get("gamma", 2.0), 0.0, xs)
+            else:
+                want = oracle.cut_objective_f64(og, OBJECTIVES[args.objective], wl.get("lambda_", 0.001), xs)
+            errs.append(abs(got - want) / max(abs(want), 1e-30))
+        objective_f64 = {"device_ms": objective_probe.get("ms"), "trajectories_checked": len(errs),
+                         "max_rel_error_vs_fp64_oracle": max(errs) if errs else None}
 
     if rank == 0:
         line = {
@@ -543,6 +580,8 @@ def gpu_arm(args):
             line["cpu_baseline"] = cpu
         if quality:
             line["quality"] = quality
+        if objective_f64:
+            line["objective_f64"] = objective_f64
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -713,6 +752,34 @@ def autograd_arm(args):
     return 0
 
 
+def rho_sweep(args):
+    """Best value per member graph after --quality-ticks ticks for each rho
+    (the reset-fraction ablation), independent trajectories; one JSON line."""
+    import torch
+    import paper_2605_06921_gb300 as mq
+    wl = WORKLOADS[args.workload]
+    G = make_graph(args.workload)
+    B = wl["batch"]
+    xd, vd = dtype_code(args.x_dtype), dtype_code(args.v_dtype or args.x_dtype)
+    out = {}
+    for rho in [float(r) for r in args.rho_sweep.split(",")]:
+        pkw = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "t_gs", "descent_cap", "init_kind",
+                                  "sigma")}
+        pkw.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), rho=rho, seed=0,
+                   objective=OBJECTIVES[args.objective])
+        g = mq.Graph(G)
+        s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **pkw))
+        s.run(args.quality_ticks)
+        vals, _ = s.best(want_bits=False)
+        per = vals.reshape(G.num_graphs, B).max(axis=1)
+        out[str(rho)] = {"best_per_graph_mean": float(per.mean()), "best_per_graph": per.tolist()}
+        s.close()
+        g.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"rho_ablation": out, "workload": wl["desc"], "ticks": args.quality_ticks}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -727,11 +794,18 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pool-k", type=int, default=0, help="pmQO pool of K sets per graph (0: Alg. 1/2)")
     ap.add_argument("--objective", default="fb", choices=sorted(OBJECTIVES), help="MaxCut relaxation")
+    ap.add_argument("--rho", type=float, default=None, help="override the workload's reset fraction rho")
+    ap.add_argument("--rho-sweep", default=None,
+                    help="comma-separated rho values: best-value runs on a paper-shaped ER workload (the rho ablation)")
     ap.add_argument("--quality-ticks", type=int, default=20000,
                     help="ticks of the best-value run on the paper-shaped ER workloads (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.rho is not None:
+        WORKLOADS[args.workload]["rho"] = args.rho
+    if args.rho_sweep:
+        return rho_sweep(args)
     if args.impl == "reference":
         if args.workload == "autograd_powerlaw":
             return reference_autograd(args)
