@@ -317,9 +317,14 @@ def profile_traffic(name, variant, sources):
     return float(t.group(1))
 
 
+STEP_SOURCES = {"smem": ("mqo_step.cu", "mqo_step.cuh", "mqo_dev.cuh"),
+                "global": ("mqo_step_generic.cu", "mqo_step.cuh", "mqo_dev.cuh")}
+
+
 def step_kernel_traffic(workload, x_dtype, variant):
     """DRAM bytes per launch of the step kernel variant (smem, smem_wide, global)."""
-    return profile_traffic(f"step_kernel_{workload}_{x_dtype}", variant, ("mqo_step.cu", "mqo_dev.cuh"))
+    src = STEP_SOURCES["global" if variant == "global" else "smem"]
+    return profile_traffic(f"step_kernel_{workload}_{x_dtype}", variant, src)
 
 
 def gpu_arm(args):
@@ -373,8 +378,7 @@ def gpu_arm(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        phase_ms, launches = s.run_timed(steps)
-        info_launches[0] = launches
+        s.run(steps)  # the captured tick graphs, as a user runs them
         e1.record()
         torch.cuda.synchronize()
         barrier()
@@ -382,6 +386,13 @@ def gpu_arm(args):
             sampler.__exit__()
         ms = e0.elapsed_time(e1)
         clocks = sampler.summary() if sampler else None
+        # per-kernel breakdown: the next ticks again, captured with an event
+        # node between consecutive kernels (the events add time of their own,
+        # so these are not the timed region)
+        phase_ticks = min(steps, 50)
+        phase_sum, launches = s.run_timed(phase_ticks)
+        phase_ms = {k: v * steps / phase_ticks for k, v in phase_sum.items()}
+        info_launches[0] = launches * steps // phase_ticks
         vals, _ = s.best(want_bits=False)
         info = s.info()
         if tuned:
@@ -644,26 +655,26 @@ def autograd_arm(args):
     gen = torch.Generator(device="cuda").manual_seed(1000 * rank)
     X = (torch.rand((G.n, B), device="cuda", generator=gen) * 2 - 1).requires_grad_(True)
     opt = mq.PGAMomentum([X], lr=wl["lr"], momentum=wl["momentum"])
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     ph = {"forward": 0.0, "backward": 0.0, "optimizer": 0.0}
 
-    def step(timed):
+    def step(ev=None):
         opt.zero_grad(set_to_none=False)
-        if timed:
+        if ev:
             ev[0].record()
         obj = mq.FbObjective.apply(X, g, lam)
-        if timed:
+        if ev:
             ev[1].record()
         obj.sum().backward()
-        if timed:
+        if ev:
             ev[2].record()
         opt.step()
-        if timed:
+        if ev:
             ev[3].record()
         return obj
 
     for _ in range(args.warmup):
-        step(False)
+        step()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -677,14 +688,14 @@ def autograd_arm(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        step(True)
-        torch.cuda.synchronize()
+    for k in range(args.steps):
+        step(evs[k])
+    e1.record()
+    torch.cuda.synchronize()
+    for ev in evs:
         ph["forward"] += ev[0].elapsed_time(ev[1])
         ph["backward"] += ev[1].elapsed_time(ev[2])
         ph["optimizer"] += ev[2].elapsed_time(ev[3])
-    e1.record()
-    torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     sampler.__exit__()
