@@ -159,9 +159,10 @@ def oracle_sample(G, wl, x_dtype, v_dtype, target_s=12.0, cores=None, pool_k=0, 
         res = pool.map(_oracle_job, jobs, chunksize=1)
     wall = time.perf_counter() - t0
     eu = sum(r[1] for r in res)
-    return dict(value=eu / wall, unit=UNIT, cores=cores, kind="oracle",
+    return dict(value=eu / wall, unit=UNIT, cores=cores, kind="oracle", single_core_value=rate1,
                 sample=f"{ntraj} trajectories x {ticks} ticks of the same workload (member graphs 0..), "
-                       f"{eu:.3e} edge-updates in {wall:.2f} s wall on {cores} processes")
+                       f"{eu:.3e} edge-updates in {wall:.2f} s wall on {cores} processes; single_core_value: "
+                       f"one trajectory of member graph 0 for 20 ticks on one core")
 
 
 def reference_arm(args):
