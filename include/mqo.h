@@ -140,8 +140,11 @@ typedef struct {
  * strictly ascending within every row; weights[nnz] int8 in {-1,+1} with
  * w_uv == w_vu, or NULL for an unweighted graph.  The pattern must be
  * symmetric with no self loops.  is_device_ptr = 1 if the three arrays are
- * device pointers (they are copied to the host once for validation).
- * Validation failures return MQO_EGRAPH.  Synchronises cuda_stream.
+ * device pointers (row_ptr is copied to the host; the entries are copied
+ * device to device).  The row pointers are checked on the host; the entries
+ * (range, self loops, order, weights, symmetry, member graphs) by a kernel
+ * after the upload when a GPU is present, else on the host, with the same
+ * messages.  Validation failures return MQO_EGRAPH.  Synchronises cuda_stream.
  */
 MQO_API mqo_status mqo_graph_create_csr(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                                 const int8_t* weights, int32_t is_device_ptr, void* cuda_stream,

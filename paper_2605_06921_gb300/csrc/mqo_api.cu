@@ -125,14 +125,25 @@ mqo_status dalloc(T** p, size_t count, std::vector<void*>* track) {
 
 size_t dtype_size(int d) { return d == DT_F32 ? 4 : 2; }
 
-// Host validation of symmetric CSR (see mqo_graph_create_csr).
-mqo_status validate(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col, const int8_t* w,
-                    const int64_t* offs, int32_t G) {
+// Host checks of the CSR structure (sizes, row pointers): O(n).
+mqo_status validate_structure(int64_t n, int64_t nnz, const int64_t* rp) {
   if (n < 1 || n >= (1LL << 31)) return fail(MQO_EINVAL, "n=%lld out of range [1, 2^31)", (long long)n);
   if (nnz < 0 || nnz >= (1LL << 31)) return fail(MQO_EINVAL, "nnz=%lld out of range [0, 2^31)", (long long)nnz);
   if (rp[0] != 0 || rp[n] != nnz) return fail(MQO_EGRAPH, "row_ptr[0] must be 0 and row_ptr[n] must be nnz");
   for (int64_t v = 0; v < n; ++v)
     if (rp[v + 1] < rp[v]) return fail(MQO_EGRAPH, "row_ptr decreases at row %lld", (long long)v);
+  return MQO_OK;
+}
+
+// Host validation of the entries of rows [r0, r1) of symmetric CSR (see
+// mqo_graph_create_csr): the message of the first bad entry of the smallest
+// bad row.  Used for the whole graph when no GPU is present, and otherwise
+// for the row the device check reports, to word the error.
+mqo_status validate(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col, const int8_t* w,
+                    const int64_t* offs, int32_t G, int64_t r0 = 0, int64_t r1 = -1) {
+  mqo_status st0 = validate_structure(n, nnz, rp);
+  if (st0 != MQO_OK) return st0;
+  if (r1 < 0) r1 = n;
   std::vector<int32_t> graph_of;
   if (offs) {
     graph_of.resize((size_t)n);
@@ -188,11 +199,12 @@ mqo_status validate(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* co
     }
   };
   const unsigned hw = std::thread::hardware_concurrency();
-  const int P = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, nnz / 65536 + 1}));
+  const int64_t nr = r1 - r0;
+  const int P = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, nnz / 65536 + 1, nr}));
   std::vector<Bad> bad((size_t)P);
   std::vector<std::thread> pool;
   for (int p = 0; p < P; ++p) {
-    const int64_t v0 = n * p / P, v1 = n * (p + 1) / P;
+    const int64_t v0 = r0 + nr * p / P, v1 = r0 + nr * (p + 1) / P;
     if (p == P - 1) check_rows(v0, v1, &bad[(size_t)p]);
     else pool.emplace_back(check_rows, v0, v1, &bad[(size_t)p]);
   }
@@ -208,25 +220,19 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   if (!out || !rp_in || (nnz > 0 && !col_in)) return fail(MQO_EINVAL, "null pointer argument");
   *out = nullptr;
   std::vector<int64_t> rp_h;
-  std::vector<int32_t> col_h;
-  std::vector<int8_t> w_h;
   const int64_t* rp = rp_in;
   const int32_t* col = col_in;
   const int8_t* w = w_in;
   if (is_dev) {
+    int nd = 0;
+    if (cudaGetDeviceCount(&nd) != cudaSuccess || nd < 1) return fail(MQO_EINVAL, "device arrays need a GPU");
+    // row pointers to the host (items, degree order); the entries are
+    // copied device to device and checked on the device
     if (n < 1 || n >= (1LL << 31)) return fail(MQO_EINVAL, "n out of range");
     rp_h.resize((size_t)n + 1);
-    col_h.resize((size_t)std::max<int64_t>(nnz, 1));
     CKG(cudaStreamSynchronize(stream));
     CKG(cudaMemcpy(rp_h.data(), rp_in, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
-    if (nnz) CKG(cudaMemcpy(col_h.data(), col_in, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
     rp = rp_h.data();
-    col = col_h.data();
-    if (w_in) {
-      w_h.resize((size_t)std::max<int64_t>(nnz, 1));
-      if (nnz) CKG(cudaMemcpy(w_h.data(), w_in, nnz, cudaMemcpyDeviceToHost));
-      w = w_h.data();
-    }
   }
   std::vector<int64_t> offs_own;
   if (!offs) {
@@ -240,7 +246,12 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
       if (offs[g + 1] <= offs[g]) return fail(MQO_EGRAPH, "member graph %d is empty", g);
     n = offs[G];
   }
-  mqo_status st = validate(n, nnz, rp, col, w, G > 1 ? offs : nullptr, G);
+  // With a GPU the entries are checked by a kernel after the upload (the
+  // host checks only the structure); without one, on the host.
+  int ndev = 0;
+  const bool on_gpu = cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
+  if (!on_gpu) cudaGetLastError();  // clear the error of the query
+  mqo_status st = on_gpu ? validate_structure(n, nnz, rp) : validate(n, nnz, rp, col, w, G > 1 ? offs : nullptr, G);
   if (st != MQO_OK) return st;
 
   auto* g = new mqo_graph_s();
@@ -292,13 +303,38 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   if ((st = dalloc(&g->d_order, (size_t)n, nullptr)) != MQO_OK) return cleanup(st);
   cudaError_t e = cudaSuccess;
   e = cudaMemcpy(g->d_rp, g->h_rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && nnz) e = cudaMemcpy(g->d_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && w && nnz) e = cudaMemcpy(g->d_w, w, nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz) e = cudaMemcpy(g->d_col, col, sizeof(int32_t) * nnz, cudaMemcpyDefault);
+  if (e == cudaSuccess && w && nnz) e = cudaMemcpy(g->d_w, w, nnz, cudaMemcpyDefault);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_off, off32.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_dmax, dmax.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cleanup(fail(MQO_ECUDA, "graph upload: %s", cudaGetErrorString(e)));
+  if (on_gpu && nnz > 0) {
+    int32_t* d_bad = nullptr;
+    if ((st = dalloc(&d_bad, 1, nullptr)) != MQO_OK) return cleanup(st);
+    int32_t bad = (int32_t)n;
+    e = cudaMemcpy(d_bad, &bad, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = launch_validate_csr(g->d_rp, g->d_col, g->d_w, g->d_off, G, (int32_t)n, d_bad, g->sms, stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) return cleanup(fail(MQO_ECUDA, "graph validation: %s", cudaGetErrorString(e)));
+    if (bad < n) {
+      // word the error from the host copy of the smallest bad row
+      if (is_dev) {
+        std::vector<int32_t> colh((size_t)nnz);
+        std::vector<int8_t> wh(w ? (size_t)nnz : 0);
+        cudaMemcpy(colh.data(), g->d_col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost);
+        if (w) cudaMemcpy(wh.data(), g->d_w, nnz, cudaMemcpyDeviceToHost);
+        st = validate(n, nnz, rp, colh.data(), w ? wh.data() : nullptr, G > 1 ? offs : nullptr, G, bad, bad + 1);
+      } else {
+        st = validate(n, nnz, rp, col, w, G > 1 ? offs : nullptr, G, bad, bad + 1);
+      }
+      if (st == MQO_OK) st = fail(MQO_EGRAPH, "row %d failed validation", bad);
+      return cleanup(st);
+    }
+  }
   *out = g;
   return MQO_OK;
 }

@@ -32,6 +32,12 @@ cudaError_t launch_objective(const SolverDev& S, double* out, cudaStream_t strea
 cudaError_t launch_ls_merge(const SolverDev& S, const TrajState* saved, cudaStream_t stream);
 cudaError_t launch_state_init(const SolverDev& S, cudaStream_t stream);
 cudaError_t launch_any_pending(const SolverDev& S, int32_t* out, cudaStream_t stream);
+// device check of the CSR entries (range, no self loop, strictly ascending
+// rows, weights in {-1,+1}, no edge between member graphs, a reverse entry
+// with the same weight): *bad_row <- the smallest row with a bad entry
+// (unchanged if none); synchronous
+cudaError_t launch_validate_csr(const int32_t* rp, const int32_t* col, const int8_t* w, const int32_t* node_off,
+                                int32_t G, int32_t n, int32_t* bad_row, int sms, cudaStream_t stream);
 cudaError_t launch_pool_ctrl(const SolverDev& S, cudaStream_t stream);
 cudaError_t launch_pool_apply(const SolverDev& S, cudaStream_t stream);
 
