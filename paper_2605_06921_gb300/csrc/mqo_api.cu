@@ -95,7 +95,6 @@ struct mqo_solver_s {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gx1 = nullptr, gx16 = nullptr;
   bool poisoned = false;
-  int grid = 1;
   size_t step_smem = 0;  // > 0: shared-memory step kernel with this much dynamic smem
   size_t disc_smem = 0;  // > 0: fused per-graph discrete kernel with this much dynamic smem
   size_t step_smem_max = 0;  // smem the shared-memory step kernel needs (0: not possible)
@@ -656,7 +655,6 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
   if ((st = dalloc(&S.any, 4, &s->allocs)) != MQO_OK) return bail(st);
   if ((st = dalloc(&s->d_pending, 1, &s->allocs)) != MQO_OK) return bail(st);
   if (cudaMallocHost(&s->h_pending, sizeof(int32_t)) != cudaSuccess) return bail(fail(MQO_ENOMEM, "pinned alloc"));
-  s->grid = std::max(1, std::min(g->num_items, g->sms * 8));
   {
     // node-parallel kernels take several CTAs per item when there are few
     // items, so that about four CTAs' worth of nodes reach every SM

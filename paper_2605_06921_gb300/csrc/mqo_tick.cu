@@ -512,7 +512,9 @@ __global__ void __launch_bounds__(kPairThreads) k_apply(SolverDev S) {
       float x;
       if (act & ACT_RESET) {
         x = base ? 1.0f : (mis ? 0.0f : -1.0f);
-        if ((int64_t)feistel_sigma(n_g, s_keys[j], vl) < s_rk[j]) x = 0.0f;
+        // v in R sets x_v = 0: only needed where x_v is not 0 already (for
+        // MIS the nodes of the base set, a few percent of the graph)
+        if (x != 0.0f && (int64_t)feistel_sigma(n_g, s_keys[j], vl) < s_rk[j]) x = 0.0f;
       } else {
         const Params& p = S.p;
         const U64x4 r = philox4x64_10(TAG_INIT, (uint64_t)s_o[j], (uint64_t)vl, 0ULL, p.seed, (uint64_t)tau);
