@@ -280,11 +280,22 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   // rows of every item by decreasing degree (ties by node id): rows that
   // walk their neighbour lists in lockstep then have nearly equal lengths
   std::vector<int32_t> order((size_t)n);
-  for (const Item& it : items) {
-    int32_t* o = order.data() + it.v0;
-    for (int32_t v = it.v0; v < it.v1; ++v) o[v - it.v0] = v;
-    std::stable_sort(o, o + (it.v1 - it.v0),
-                     [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+  {
+    auto sort_items = [&](size_t i0, size_t i1) {
+      for (size_t i = i0; i < i1; ++i) {
+        const Item& it = items[i];
+        int32_t* o = order.data() + it.v0;
+        for (int32_t v = it.v0; v < it.v1; ++v) o[v - it.v0] = v;
+        std::stable_sort(o, o + (it.v1 - it.v0),
+                         [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+      }
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t P = std::max<size_t>(1, std::min<size_t>({(size_t)(hw ? hw : 1), 32, items.size() / 64 + 1}));
+    std::vector<std::thread> th;
+    for (size_t p = 1; p < P; ++p) th.emplace_back(sort_items, items.size() * p / P, items.size() * (p + 1) / P);
+    sort_items(0, items.size() / P);
+    for (auto& t : th) t.join();
   }
   g->num_items = (int32_t)items.size();
   g->h_items = items;
