@@ -50,3 +50,37 @@ def test_invalid_graph_is_rejected_without_gpu_work():
     st = lib.mqo_graph_create_csr(2, 2, rp.ctypes.data_as(ctypes.c_void_p), col.ctypes.data_as(ctypes.c_void_p),
                                   None, 0, None, ctypes.byref(h))
     assert st == -2 and b"self loop" in lib.mqo_last_error()
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets of the
+    C structures in include/mqo.h (compiled here with the host compiler)."""
+    import shutil
+    import subprocess
+    import paper_2605_06921_gb300 as mq
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no host C compiler")
+    fields = {"mqo_params": [f for f, _ in mq.Params._fields_],
+              "mqo_traj_info": [f for f, _ in mq.TrajInfo._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mqo.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            st, name, val = ln.split()
+            got[(st, name)] = int(val)
+    for st, cls in (("mqo_params", mq.Params), ("mqo_traj_info", mq.TrajInfo)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
