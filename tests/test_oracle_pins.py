@@ -473,3 +473,37 @@ def test_init_distributions():
     base = 1 - d / d.max()
     assert abs(float(np.mean(xd - base))) < 0.01
     assert abs(float(np.std(xd - base)) - 0.05) < 0.01
+
+
+def test_oracle_struct_layouts_match_the_c_source(tmp_path):
+    """The oracle binding's ctypes structures have the sizes and field offsets
+    of the C structures of oracle/mqo_oracle.c."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pairs = {"orc_params": oracle.OrcParams, "orc_state": oracle.OrcState, "orc_pool": oracle.OrcPool,
+             "orc_graph": oracle.OrcGraph}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{root}/oracle/mqo_oracle.c"', "int main(void) {"]
+    for st, cls in pairs.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-o", str(exe), str(src), "-lm"], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if ln:
+            st, name, val = ln.split()
+            got[(st, name)] = int(val)
+    for st, cls in pairs.items():
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
