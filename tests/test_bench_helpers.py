@@ -1,0 +1,63 @@
+"""Host-side helpers of bench.py: the algorithmic byte counts of the
+roofline, and the DRAM traffic read from a committed profile summary, which
+must be dropped as soon as a profiled source file changes."""
+import hashlib
+import os
+
+import numpy as np
+
+import bench
+import mqo_inputs as mi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_algorithmic_bytes_formula():
+    G = mi.pack([mi.erdos_renyi(50, 0.2, 1), mi.erdos_renyi(40, 0.1, 2)])
+    B = 32
+    got = bench.algorithmic_bytes_per_step(G, B, 2, 2)
+    # CSR once (int32 col + row_ptr), x and V read + written, one rounding word per node
+    want = G.nnz * 4 + (G.n + 1) * 4 + 2 * G.n * B * 2 + 2 * G.n * B * 2 + G.n * 4
+    assert got == want
+    assert bench.fb_kernel_bytes(G, 64, True) - bench.fb_kernel_bytes(G, 64, False) == G.n * 64 * 4
+
+
+def test_profile_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    srcs = ("mqo_step.cu", "mqo_step.cuh", "mqo_dev.cuh")
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(os.path.join(ROOT, "paper_2605_06921_gb300", "csrc", f), "rb").read())
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "x.txt").write_text(f"source_sha256: {h.hexdigest()}\ndram_bytes_per_launch[smem]: 1.5e8\n")
+    (prof / "y.txt").write_text(f"source_sha256: {'0' * 64}\ndram_bytes_per_launch[smem]: 1.5e8\n")
+    # read the summaries from the temporary folder, the sources from the repository
+    real_join = os.path.join
+
+    def join(*parts):
+        if len(parts) >= 2 and parts[0] == bench.ROOT and parts[1] == "profiles":
+            return real_join(str(prof), *parts[2:])
+        return real_join(*parts)
+    monkeypatch.setattr(bench.os.path, "join", join)
+    assert bench.profile_traffic("x", "smem", srcs) == 1.5e8
+    assert bench.profile_traffic("y", "smem", srcs) is None      # the kernel changed since the capture
+    assert bench.profile_traffic("x", "global", srcs) is None    # no figure for that variant
+    assert bench.profile_traffic("missing", "smem", srcs) is None
+
+
+def test_committed_profiles_carry_traffic_for_the_current_sources():
+    """The summaries under profiles/ were captured from the current kernel
+    sources (their recorded hash matches), so the bench reports their DRAM
+    traffic."""
+    assert bench.step_kernel_traffic("mis_batched", "bf16", "smem") is not None
+    assert bench.step_kernel_traffic("maxcut_regular", "bf16", "global") is not None
+    assert bench.profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_units", ("mqo_grad.cu", "mqo_dev.cuh")) \
+        is not None
+
+
+def test_reference_sample_is_the_oracle_on_a_bounded_sample():
+    G = mi.pack([mi.erdos_renyi(60, 0.15, k) for k in range(3)])
+    wl = dict(bench.WORKLOADS["mis_batched"], batch=4)
+    r = bench.oracle_sample(G, wl, 1, 1, target_s=0.2, cores=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0 and r["single_core_value"] > 0
+    assert np.isfinite(r["value"])
