@@ -58,6 +58,12 @@ def test_committed_profiles_carry_traffic_for_the_current_sources():
 def test_reference_sample_is_the_oracle_on_a_bounded_sample():
     G = mi.pack([mi.erdos_renyi(60, 0.15, k) for k in range(3)])
     wl = dict(bench.WORKLOADS["mis_batched"], batch=4)
-    r = bench.oracle_sample(G, wl, 1, 1, target_s=0.2, cores=2)
+    try:
+        r = bench.oracle_sample(G, wl, 1, 1, target_s=0.2, cores=2)
+    finally:  # no pool threads left behind for later tests that fork
+        for p in bench._POOLS.values():
+            p.terminate()
+            p.join()
+        bench._POOLS.clear()
     assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0 and r["single_core_value"] > 0
     assert np.isfinite(r["value"])
