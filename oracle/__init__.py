@@ -106,6 +106,10 @@ def lib():
             _lib.orc_state_init.argtypes = [P]
             _lib.orc_run_trajectory.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, P, P, P, P, P, P, P,
                                                 C.c_int64]
+            _lib.orc_ls_mis_sequential.restype = C.c_int64
+            _lib.orc_ls_mis_sequential.argtypes = [P, P, P]
+            _lib.orc_ls_cut_sequential.restype = C.c_int64
+            _lib.orc_ls_cut_sequential.argtypes = [P, P]
             _lib.orc_pool_pick.restype = C.c_int64
             _lib.orc_pool_pick.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_int64]
             _lib.orc_run_pool.argtypes = [P, P, C.c_int64, C.c_int32, C.c_int64, C.c_int32, P, P, P, P, P, P, P,
@@ -293,6 +297,21 @@ class Trajectory:
     @property
     def state(self):
         return self.st.as_dict()
+
+
+def ls_mis_sequential(g: Graph, z):
+    """OneTwoSwap in the paper's scan order; returns (z, swaps, adds)."""
+    z = np.ascontiguousarray(z, dtype=np.uint8).copy()
+    adds = C.c_int64()
+    k = lib().orc_ls_mis_sequential(g.ref(), _ptr(z), C.byref(adds))
+    return z, int(k), adds.value
+
+
+def ls_cut_sequential(g: Graph, z):
+    """OneTwoFlip in the paper's scan order; returns (z, moves)."""
+    z = np.ascontiguousarray(z, dtype=np.uint8).copy()
+    k = lib().orc_ls_cut_sequential(g.ref(), _ptr(z))
+    return z, int(k)
 
 
 def pool_pick(seed, traj, outer, rnd, count):

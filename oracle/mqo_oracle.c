@@ -24,6 +24,8 @@
  *                            uniformity by chi-square
  *   repair / local search    pinned: invariants (independent, maximal,
  *                            swap-free / flip-free, exact gains), brute force
+ *   orc_ls_*_sequential      pinned: the same invariants, move counts against
+ *                            the value gained
  *   run_trajectory           pinned through its parts + brute-force bound
  */
 #include <math.h>
@@ -665,6 +667,84 @@ ORC_API int64_t orc_round_flip2(const orc_graph* g, uint8_t* z) {
   }
   free(gain); free(owner); free(pb); free(commit);
   return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* Local search in the paper's order (Sec. 4: scan the nodes in index   */
+/* order and restart after each move), for cross-checking the round-    */
+/* based variant above: both must end at points with the same defining  */
+/* properties.  Returns the number of moves; *adds (MIS) counts the      */
+/* free nodes added.                                                     */
+/* ------------------------------------------------------------------ */
+
+/* OneTwoSwap: add free nodes (lowest index first) until maximal; then the
+ * first set node v (index order) with a pair of non-adjacent tight
+ * neighbours (the first such pair in CSR order of N(v)) swaps v for the
+ * pair (Def. 2.3); repeat until no swap exists. */
+ORC_API int64_t orc_ls_mis_sequential(const orc_graph* g, uint8_t* z, int64_t* adds) {
+  const int64_t n = g->n;
+  int64_t moves = 0, added = 0;
+  int32_t* cnt = malloc(((size_t)n + 1) * sizeof(int32_t));
+  for (;;) {
+    for (int64_t v = 0; v < n; ++v) { /* completion */
+      if (z[v]) continue;
+      int any = 0;
+      for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1] && !any; ++j) any = z[g->col[j]];
+      if (!any) { z[v] = 1; ++added; }
+    }
+    for (int64_t v = 0; v < n; ++v) {
+      cnt[v] = 0;
+      for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) cnt[v] += z[g->col[j]];
+    }
+    int64_t fa = -1, fb = -1, fv = -1;
+    for (int64_t v = 0; v < n && fv < 0; ++v) {
+      if (!z[v]) continue;
+      for (int64_t i = g->row_ptr[v]; i < g->row_ptr[v + 1] && fv < 0; ++i) {
+        const int32_t a = g->col[i];
+        if (z[a] || cnt[a] != 1) continue;
+        for (int64_t j = i + 1; j < g->row_ptr[v + 1]; ++j) {
+          const int32_t c = g->col[j];
+          if (z[c] || cnt[c] != 1 || adjacent(g, a, c)) continue;
+          fa = a; fb = c; fv = v;
+          break;
+        }
+      }
+    }
+    if (fv < 0) break;
+    z[fv] = 0; z[fa] = 1; z[fb] = 1;
+    ++moves;
+  }
+  free(cnt);
+  if (adds) *adds = added;
+  return moves;
+}
+
+/* OneTwoFlip: the first node (index order) with a positive 1-flip gain
+ * changes side (Def. 2.4), repeated until none; then the first edge (a,b),
+ * a < b in CSR order, across the cut with gain_a + gain_b + 2 w_ab > 0
+ * swaps sides (Def. 2.5), and the 1-flips resume; until neither applies. */
+ORC_API int64_t orc_ls_cut_sequential(const orc_graph* g, uint8_t* z) {
+  const int64_t n = g->n;
+  int64_t moves = 0;
+  int64_t* gain = malloc(((size_t)n + 1) * sizeof(int64_t));
+  for (;;) {
+    gains(g, z, gain);
+    int64_t f = -1;
+    for (int64_t v = 0; v < n && f < 0; ++v) if (gain[v] > 0) f = v;
+    if (f >= 0) { z[f] ^= 1; ++moves; continue; }
+    int64_t fa = -1, fb = -1;
+    for (int64_t a = 0; a < n && fa < 0; ++a)
+      for (int64_t j = g->row_ptr[a]; j < g->row_ptr[a + 1]; ++j) {
+        const int32_t b = g->col[j];
+        if (b <= a || z[b] == z[a]) continue;
+        if (gain[a] + gain[b] + 2 * (int64_t)wt(g, j) > 0) { fa = a; fb = b; break; }
+      }
+    if (fa < 0) break;
+    z[fa] ^= 1; z[fb] ^= 1;
+    ++moves;
+  }
+  free(gain);
+  return moves;
 }
 
 /* counts after a discrete round: MIS (size, conflicting nodes, free);
