@@ -47,6 +47,9 @@ WORKLOADS = {
                         gamma=2.0, rho=0.6, t_gs=60, descent_cap=50, init_kind=1, sigma=0.1),
     "maxcut_regular": dict(desc="MaxCut f_B: random 3-regular n=100000, B=128", problem=1, batch=128, alpha=0.0025,
                            momentum=0.8, lambda_=0.001, rho=0.8, t_gs=90, descent_cap=200, init_kind=1, sigma=0.1),
+    "maxcut_regular_signed": dict(desc="MaxCut f_B: random 3-regular n=100000, edge weights uniform in {-1,+1}, "
+                                       "B=128", problem=1, batch=128, alpha=0.0025, momentum=0.8, lambda_=0.001,
+                                  rho=0.8, t_gs=90, descent_cap=200, init_kind=1, sigma=0.1),
     "mis_scale": dict(desc="MIS at scale: ER n=1e7 mean degree 10, B=16", problem=0, batch=16, alpha=0.8,
                       momentum=0.75, gamma=2.0, rho=0.5, t_gs=60, descent_cap=50, init_kind=1, sigma=0.1),
     # the paper's ER setting (n, d) = (1000, 100) with its hyperparameter rows
@@ -75,6 +78,8 @@ def make_graph(name):
         return mi.workload_mis_batched()
     if name == "maxcut_regular":
         return mi.workload_maxcut_regular()
+    if name == "maxcut_regular_signed":
+        return mi.workload_maxcut_regular(signed=True)
     if name == "mis_scale":
         return mi.workload_mis_scale()
     if name in ("er_mis_1000_100", "er_maxcut_1000_100"):
