@@ -1,15 +1,18 @@
 // mqo_tick.cu -- the per-trajectory machine of Alg. 1 / Alg. 2 on the GPU.
 //
-// One tick = control (one thread per trajectory) -> apply (accept copies,
+// One tick = (pool mode: the graphs' pool decisions, mqo_pool.cu ->)
+// control (one thread, or one warp, per trajectory) -> apply (accept copies,
 // resets, initialisations) -> fused descent step -> discrete round passes
-// A, B and the count pass C -> tick end.  The control kernel decides, from
-// the exact counters of the previous tick, what each trajectory does now;
-// the node-parallel kernels then act on (node, trajectory) pairs.  Member
+// A, B and the count pass C (or the fused per-graph kernel,
+// mqo_disc_graph.cu) -> tick end.  The control kernel decides, from the
+// exact counters of the previous tick, what each trajectory does now; the
+// node-parallel kernels then act on (node, trajectory) pairs.  Member
 // graphs with nothing to do in a pass are skipped through per-graph tick
 // stamps written by the control kernel.
 //
 // Pair kernels map thread -> (node v, trajectory b), trajectory fastest,
-// one CTA per item (<= 256 nodes of one member graph).  The lanes that
+// one CTA per item (<= 256 nodes of one member graph), or a slice of an item
+// per CTA when there are few items (item_slice).  The lanes that
 // share one bit word of a node (G = min(B,32) lanes) form a group; MIS set
 // logic is done on whole words: the group splits v's neighbour list, ORs
 // (or once/twice-accumulates) the neighbours' words and reduces by shuffles.
