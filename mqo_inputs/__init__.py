@@ -13,7 +13,6 @@ whose streams are identical on x86-64 and aarch64.
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import numpy as np
 
