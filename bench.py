@@ -261,6 +261,9 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            # one more sample after the timed region, so that the samples
+            # bracket it even when it is shorter than the sampling interval
+            time.sleep(0.25)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
