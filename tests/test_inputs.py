@@ -80,3 +80,13 @@ def test_signed_weights_are_symmetric():
     w = np.where(rng.random(int(keep.sum())) < 0.5, -1, 1)
     H = mi.from_edges(G.n, rows[keep], cols[keep], w)
     assert_valid(H)
+
+
+def test_random_regular_rejects_odd_stub_count_and_signs_edges():
+    with pytest.raises(ValueError):
+        mi.random_regular(11, 3, 0)
+    G = mi.random_regular(200, 3, 4, signed_weights=True)
+    assert_valid(G)
+    w = G.weights
+    assert set(np.unique(w).tolist()) == {-1, 1}
+    assert 0.35 < (w == 1).mean() < 0.65

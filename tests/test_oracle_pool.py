@@ -110,3 +110,24 @@ def test_pool_of_one_is_the_single_trajectory_machine(problem):
     assert len(common) > 20
     for key in common:  # the best set when round (o, r) starts, and the descents before it
         assert a[key] == b[key], (key, a[key], b[key])
+
+
+@pytest.mark.parametrize("problem", [0, 1])
+def test_pool_without_reset_rounds_goes_straight_to_local_search(problem):
+    """T_gs = 0: after the first merge the graph runs local search (step 13)
+    and then fresh initialisations; the pool invariants still hold and the
+    best value never decreases."""
+    G = mi.erdos_renyi(40, 0.15, 3)
+    g = og(G)
+    pg = oracle.PoolGraph(g, _pool_params(problem, 3, 4, t_gs=0), 0, 4)
+    last = oracle.INT64_MIN
+    for _ in range(10):
+        pg.run(30)
+        vals, bits = pg.members()
+        assert all(vals[i] >= vals[i + 1] for i in range(len(vals) - 1))
+        best = pg.pool.best
+        assert best >= last
+        last = best
+        for b in range(4):
+            assert pg.state(b)["r"] == 0          # no reset round is ever started
+    assert pg.pool.merges > 0
