@@ -26,6 +26,11 @@
  *                            swap-free / flip-free, exact gains), brute force
  *   orc_ls_*_sequential      pinned: the same invariants, move counts against
  *                            the value gained
+ *   orc_init_x               pinned: exact projected centres of Alg. 1/2
+ *                            step 2 at sigma = 0, noise mean and spread
+ *   reset_from / accept      pinned through the machine: the first step after
+ *                            a reset starts from the point of Alg. 1/2 steps
+ *                            6-8; equal-valued candidates leave the best set
  *   run_trajectory           pinned through its parts + brute-force bound
  */
 #include <math.h>
