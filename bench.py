@@ -334,12 +334,46 @@ def profile_traffic(name, variant, sources):
     t = re.search(r"dram_bytes_per_launch\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", txt)
     if not m or not t:
         return None
-    h = hashlib.sha256()
-    for f in sources:
-        h.update(open(os.path.join(ROOT, "paper_2605_06921_gb300", "csrc", f), "rb").read())
-    if h.hexdigest() != m.group(1):
+    if source_hash(sources) != m.group(1):
         return None
     return float(t.group(1))
+
+
+def code_text(src: str) -> str:
+    """C / CUDA source without its comments and with every run of white
+    space reduced to one blank: what the compiler sees of the code, so that
+    a comment edit leaves the hash of a profiled kernel unchanged."""
+    out = []
+    i, n = 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+            out.append(" ")
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def source_hash(sources) -> str:
+    """sha256 over the code text (code_text) of csrc/<f> for f in sources, in order."""
+    h = hashlib.sha256()
+    for f in sources:
+        txt = open(os.path.join(ROOT, "paper_2605_06921_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(code_text(txt).encode())
+    return h.hexdigest()
 
 
 STEP_SOURCES = {"smem": ("mqo_step.cu", "mqo_step.cuh", "mqo_dev.cuh"),

@@ -4,9 +4,9 @@
  * Method: "Mutation-Guided Differentiable Quadratic Combinatorial
  * Optimization" (mQO).  The library runs batched projected momentum
  * gradient ascent on the box-relaxed MIS objective
- *     h(x)   = 1^T x - (gamma/2) x^T A x,   x in [0,1]^n   (Eq. MIS QUBO)
+ *     h(x)   = 1^T x - (gamma/2) x^T A x,   x in [0,1]^n   (Eq. 3)
  * and the perturbed-bias MaxCut objective
- *     f_B(x) = -lambda 1^T x - x^T A x,     x in [-1,1]^n  (Eq. adj_lin_two_props)
+ *     f_B(x) = -lambda 1^T x - x^T A x,     x in [-1,1]^n  (Eq. 7)
  * fused with threshold rounding and exact integer evaluation, inside the
  * per-trajectory mutation/reset/local-search machine of Alg. 1 (MIS) and
  * Alg. 2 (MaxCut), B independent trajectories per graph (pmQO, Alg. 3/4).
@@ -61,8 +61,8 @@ typedef enum {
 
 typedef enum { MQO_MIS = 0, MQO_MAXCUT = 1 } mqo_problem;
 /* MaxCut relaxation descended by the solver (Sec. 3):
- *   MQO_OBJ_FB  f_B(x) = -lambda 1'x - x'Ax        (Eq. adj_lin_two_props; the default)
- *   MQO_OBJ_FL  f_L(x) = 1/4 x'Lx, L = D - A       (Eq. Cut QUBO)
+ *   MQO_OBJ_FB  f_B(x) = -lambda 1'x - x'Ax        (Eq. 7; the default)
+ *   MQO_OBJ_FL  f_L(x) = 1/4 x'Lx, L = D - A       (Eq. 4)
  *   MQO_OBJ_FP  f_P(x) = x'(L + lambda I)x         (perturbed Laplacian)
  *   MQO_OBJ_FA  f_A(x) = -x'Ax                     (adjacency form)
  * Each equals an affine function of the cut on {-1,1}^n; they differ in
@@ -77,7 +77,7 @@ typedef enum { MQO_PH_DESCENT = 0, MQO_PH_REPAIR = 1, MQO_PH_LS = 2, MQO_PH_WAIT
 
 /*
  * Solver parameters.  Paper symbols: alpha (step size), momentum (MGA,
- * Sec. 5 and App. F), gamma > 1 (edge penalty of h, Eq. MIS QUBO),
+ * Sec. 5 and App. F), gamma > 1 (edge penalty of h, Eq. 3),
  * lambda in (0,2) (bias of f_B, Thm 3.6; 0.001 in Sec. 5), rho in (0,1)
  * (reset fraction, |R| = floor(rho n), Sec. 4), t_gs (global-reset rounds
  * per outer iteration, Alg. 1 step 5), sigma (init noise std, Alg. 1
@@ -186,8 +186,7 @@ MQO_API mqo_status mqo_solver_destroy(mqo_solver s);
 MQO_API mqo_status mqo_init(mqo_solver s);
 
 /*
- * nsteps plain fused steps for every trajectory (the gradient of Eq. MIS
- * QUBO / Eq. adj_lin_two_props as a CSR SpMM, the momentum step, the
+ * nsteps plain fused steps for every trajectory (the gradient of Eq. 3 / Eq. 7 as a CSR SpMM, the momentum step, the
  * projection onto the box, threshold rounding of Sec. 3 and the exact
  * evaluation of the rounded point, all in one kernel per step).  The
  * machine state is left untouched; mqo_step_stats reads the evaluation of
@@ -208,7 +207,7 @@ MQO_API mqo_status mqo_step_stats(mqo_solver s, int64_t* value, int64_t* a, int6
  * nticks ticks of the full per-trajectory machine (Alg. 1 / Alg. 2 with a
  * tick budget in place of the wall clock): each tick every trajectory
  * takes one descent step or one discrete round; descents end at the
- * fixed-point test (Eq. MIS checking; for MaxCut the fixed point of the
+ * fixed-point test (Eq. 8; for MaxCut the fixed point of the
  * solver's relaxation, e.g. f_B, Thm 3.6) or at
  * descent_cap; strict acceptance (Alg. 1 steps 4/10); reset rounds from the
  * best set (steps 6-8); local search after t_gs rounds (step 11); a fresh
@@ -330,8 +329,8 @@ MQO_API mqo_status mqo_get_v(mqo_solver s, void* v_out);
 
 /*
  * Relaxed objective of the current x per trajectory, in double precision
- * (h of Eq. MIS QUBO, or the solver's MaxCut relaxation: f_B of
- * Eq. adj_lin_two_props, f_L, f_P or f_A of Sec. 3), into device double
+ * (h of Eq. 3, or the solver's MaxCut relaxation: f_B of
+ * Eq. 7, f_L, f_P or f_A of Sec. 3), into device double
  * out[G*B].  (Ax)_v is accumulated in float32 in CSR order; products and
  * sums are in double.
  */
@@ -359,10 +358,10 @@ MQO_API mqo_status mqo_spmm_grad(mqo_graph g, const float* X, const float* gout,
 /*
  * Same result as mqo_spmm_grad, but the call allocates nothing.  The paper
  * has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc during the call -- code issuing work while a stream is being
- * captured into a CUDA graph, applications whose device memory is already
- * held by their own pool or allocator, and loops that must not pay for an
- * allocation.  mqo_spmm_grad keeps a scratch buffer for the partial sums of
+ * cudaMalloc during the call -- applications whose device memory is already
+ * held by their own pool or allocator, and loops that must not pay for
+ * cudaMalloc / cudaFree, which can synchronise the device.  mqo_spmm_grad
+ * keeps a scratch buffer for the partial sums of
  * long rows and allocates (or grows) it on first use; this variant keeps
  * those partial sums in one static device array of 4 MiB (1,048,576 32-bit
  * words) that every GPU loading the library holds until the process exits.

@@ -79,8 +79,8 @@ typedef struct {
   int32_t repair;
   uint64_t seed;
   int32_t pool_k;     /* 0: independent trajectories (Alg. 1/2); K >= 1: pmQO pool (Alg. 3/4) */
-  int32_t objective;  /* MaxCut relaxation: ORC_F_B (Eq. adj_lin_two_props), ORC_F_L (Eq. Cut QUBO),
-                         ORC_F_P (Eq. perturbed Laplacian cut), ORC_F_A (Eq. adj cut formulation) */
+  int32_t objective;  /* MaxCut relaxation: ORC_F_B (Eq. 7), ORC_F_L (Eq. 4),
+                         ORC_F_P (Eq. 5), ORC_F_A (Eq. 6) */
 } orc_params;
 
 /* Per-trajectory machine state, mirrored field by field for the tests. */
@@ -314,8 +314,8 @@ ORC_API void orc_reset_mask(int64_t n, double rho, uint64_t seed, int64_t traj, 
 }
 
 /* ------------------------------------------------------------------ */
-/* Exact evaluation of binary points (Def. 2.1/2.2, Eq. (MIS ILP),      */
-/* Eq. (cut ILP), checker Eq. (MIS checking)).                          */
+/* Exact evaluation of binary points (Def. 2.1/2.2, Eq. 1, Eq. 2,       */
+/* checker Eq. 8).                                                      */
 /* ------------------------------------------------------------------ */
 static int8_t wt(const orc_graph* g, int64_t j) { return g->w ? g->w[j] : (int8_t)1; }
 
@@ -424,8 +424,8 @@ static uint8_t round_z(const orc_params* p, float x) {
 /* ------------------------------------------------------------------ */
 /* One projected momentum-gradient-ascent step (Sec. 3 PGA update,      */
 /* MGA as used in Sec. 5), heavy-ball form V <- mu V + alpha grad,       */
-/* x <- Pi(x + V).  Gradients: MIS grad h = 1 - gamma A x (Eq. MIS QUBO);*/
-/* MaxCut grad f_B = -lambda 1 - 2 A x (Eq. adj_lin_two_props).          */
+/* x <- Pi(x + V).  Gradients: MIS grad h = 1 - gamma A x (Eq. 3);*/
+/* MaxCut grad f_B = -lambda 1 - 2 A x (Eq. 7).          */
 /* (Ax)_v is accumulated in float in CSR order, one rounding per add.    */
 /* z of the incoming x is evaluated exactly (checker / cut).             */
 /* ------------------------------------------------------------------ */
@@ -771,7 +771,7 @@ static void disc_counts(const orc_graph* g, const orc_params* p, const uint8_t* 
 /* descent step (Alg. 1 steps 3 and 9), or one discrete round (repair of */
 /* a capped descent, or one OneTwoSwap / OneTwoFlip round of step 11).   */
 /* Descent ends when z(x_t) passes the fixed-point test (MIS checker,    */
-/* Eq. MIS checking; MaxCut f_B fixed point, Thm 3.6) or after           */
+/* Eq. 8; MaxCut f_B fixed point, Thm 3.6) or after           */
 /* descent_cap steps.  Acceptance is strict (steps 4 and 10).  After     */
 /* acceptance: reset round r+1 from the best set (steps 6-8), or after   */
 /* T_gs rounds local search (step 11), then a new outer iteration        */
@@ -1232,8 +1232,8 @@ ORC_API void orc_run_pool(const orc_graph* g, const orc_params* p, int64_t traj0
 }
 
 /* ------------------------------------------------------------------ */
-/* Relaxed objectives in double precision (Eq. MIS QUBO, Eq.            */
-/* adj_lin_two_props) and the f_B gradient -lambda 1 - 2 A x.           */
+/* Relaxed objectives in double precision (Eq. 3, Eq. 7) and the f_B  */
+/* gradient -lambda 1 - 2 A x.                                         */
 /* ------------------------------------------------------------------ */
 ORC_API double orc_objective_f64(const orc_graph* g, int32_t problem, double gamma, double lambda_, const double* x) {
   double lin = 0.0, quad = 0.0;

@@ -398,7 +398,7 @@ def _autograd():
     import torch
 
     class FbObjective(torch.autograd.Function):
-        """f_B(X) per column (Eq. adj_lin_two_props) with the fused SpMM gradient as backward."""
+        """f_B(X) per column (Eq. 7) with the fused SpMM gradient as backward."""
 
         @staticmethod
         def forward(ctx, X, graph, lambda_):

@@ -68,6 +68,10 @@ struct mqo_graph_s {
   float* d_scratch = nullptr;
   size_t scratch_floats = 0;
   int sms = 152;
+  // rows longer than 512 entries and their 512-entry chunks (counted once at
+  // creation, for the allocation-free gradient's capacity check)
+  int32_t long_rows = 0;
+  int64_t long_chunks = 0;
 
   GraphDev dev() const {
     GraphDev g;
@@ -262,6 +266,13 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
   g->h_rp.resize((size_t)n + 1);
   for (int64_t v = 0; v <= n; ++v) g->h_rp[(size_t)v] = (int32_t)rp[v];
+  for (int64_t v = 0; v < n; ++v) {
+    const int64_t d = rp[v + 1] - rp[v];
+    if (d > 512) {
+      g->long_rows += 1;
+      g->long_chunks += (d + 511) / 512;
+    }
+  }
   std::vector<int32_t> off32((size_t)G + 1), dmax((size_t)G, 0);
   std::vector<Item> items;
   for (int32_t k = 0; k <= G; ++k) off32[(size_t)k] = (int32_t)offs[k];
@@ -478,17 +489,9 @@ void graph_csr_view(mqo_graph_s* g, GraphCsrView* out) {
   out->col = g->d_col;
   out->w = g->d_w;
   out->n = (int32_t)g->n;
-  int32_t rows = 0;
-  int64_t chunks = 0;
-  for (int64_t v = 0; v < g->n; ++v) {
-    const int32_t d = g->h_rp[(size_t)v + 1] - g->h_rp[(size_t)v];
-    if (d > 512) {
-      rows += 1;
-      chunks += (d + 511) / 512;
-    }
-  }
-  out->long_rows = rows;
-  out->long_chunks = chunks;
+  out->long_rows = g->long_rows;
+  out->long_chunks = g->long_chunks;
+  out->sms = g->sms;
 }
 
 mqo_status set_last_error(mqo_status status, const char* msg) {

@@ -14,8 +14,8 @@ namespace mqo {
 
 enum : int { PROB_MIS = 0, PROB_MAXCUT = 1 };
 enum : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
-// MaxCut relaxations of Sec. 3: f_B (Eq. adj_lin_two_props, the default),
-// f_L (Eq. Cut QUBO), f_P (perturbed Laplacian), f_A (adjacency form)
+// MaxCut relaxations of Sec. 3: f_B (Eq. 7, the default),
+// f_L (Eq. 4), f_P (perturbed Laplacian), f_A (adjacency form)
 enum : int { OBJ_FB = 0, OBJ_FL = 1, OBJ_FP = 2, OBJ_FA = 3 };
 // PH_WAIT (pool mode): the trajectory holds a finished set until every
 // trajectory of its graph has one (the batch of Alg. 3/4 steps 3-4)

@@ -1,7 +1,7 @@
 // mqo_grad.cu -- f_B forward / backward on a float32 block, and the
 // projected momentum / Adam updates that drive it (autograd path).
 //
-// f_B(x) = -lambda 1^T x - x^T A x (Eq. adj_lin_two_props), per column b of
+// f_B(x) = -lambda 1^T x - x^T A x (Eq. 7), per column b of
 // X (n x B, node-major); grad f_B = -lambda 1 - 2 A x (proof of Thm 3.6).
 //
 // Power-law graphs have rows of very different length.  Rows of degree up

@@ -70,6 +70,7 @@ struct GraphCsrView {
   int32_t n;
   int32_t long_rows;
   int64_t long_chunks;
+  int32_t sms;  // multiprocessors of the device the graph was created on
 };
 
 }  // namespace mqo

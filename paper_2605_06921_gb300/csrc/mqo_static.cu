@@ -1,13 +1,12 @@
 // mqo_static.cu -- gradient of f_B with no allocation: scratch lives in a
 // fixed-size static device array owned by the library.
 //
-// For callers that cannot allocate device memory during the call: code
-// running while a CUDA stream is being captured into a graph (cudaMalloc is
-// not a capturable operation), applications whose memory is held entirely
-// by their own pool or allocator (e.g. a framework's caching allocator that
-// has reserved the device), and latency-sensitive loops that must not pay
-// for an allocation.  The regular mqo_spmm_grad keeps a per-graph scratch
-// buffer and its chunk plan, both allocated on first use.
+// For callers that cannot allocate device memory during the call:
+// applications whose device memory is held entirely by their own pool or
+// allocator (e.g. a framework's caching allocator that has reserved the
+// device), and loops that must not pay for cudaMalloc / cudaFree, which can
+// synchronise the device.  The regular mqo_spmm_grad keeps a per-graph
+// scratch buffer and its chunk plan, both allocated on first use.
 //
 // This variant computes the same gradient G = gout * (-lambda - 2 A X):
 //   pass 1: every row of degree <= kSplitS is accumulated whole (CSR order)
@@ -179,10 +178,10 @@ extern "C" mqo_status mqo_spmm_grad_static(mqo_graph g, const float* X, const fl
   StaticArgs a{csr.row_ptr, csr.col, csr.w, csr.n, X, B, lambda_, gout, G, scratch, csr.long_rows,
                (int64_t)csr.long_chunks * B};
   const int64_t total = (int64_t)csr.n * B;
-  const int grid1 = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  const int grid1 = (int)std::min<int64_t>((total + 255) / 256, (int64_t)csr.sms * 32);
   k_static_pass1<<<grid1, 256, 0, s>>>(a);
   if (csr.long_rows > 0) {
-    const int grid2 = std::min(csr.long_rows, 152 * 8);
+    const int grid2 = std::min(csr.long_rows, csr.sms * 8);
     k_static_pass2<<<grid2, 256, 0, s>>>(a);
     k_static_pass3<<<grid2, 256, 0, s>>>(a);
   }

@@ -5,15 +5,15 @@
 //
 // For every node v and trajectory b of a stepping trajectory:
 //   (A x)_vb  = sum over the CSR row of v, in row order, of w_vu x_ub (float32)
-//   grad      = 1 - gamma (A x)_vb              (h, Eq. MIS QUBO)
-//             | -lambda - 2 (A x)_vb            (f_B, Eq. adj_lin_two_props)
+//   grad      = 1 - gamma (A x)_vb              (h, Eq. 3)
+//             | -lambda - 2 (A x)_vb            (f_B, Eq. 7)
 //             | or the gradient of f_L, f_P, f_A (Sec. 3), selected by
 //               `objective`; f_L and f_P also use the weighted degree d_v
 //   V'        = mu V + alpha grad               (momentum ascent, Sec. 5)
 //   x'        = Pi_box(x + V')                  (projection of Sec. 3)
 // and, from the same neighbour gather, the exact evaluation of the rounded
 // incoming point z = [x > 0.5] (MIS) or [x > 0] (MaxCut): set size,
-// conflicting and uncovered nodes (checker, Eq. MIS checking), or cut,
+// conflicting and uncovered nodes (checker, Eq. 8), or cut,
 // nodes violating the fixed-point condition of the selected relaxation and
 // positive-gain nodes.
 // The rounding of x' is written next to x' (ZX), so the next step and the

@@ -1,7 +1,6 @@
 """Host-side helpers of bench.py: the algorithmic byte counts of the
 roofline, and the DRAM traffic read from a committed profile summary, which
 must be dropped as soon as a profiled source file changes."""
-import hashlib
 import os
 
 import numpy as np
@@ -24,12 +23,10 @@ def test_algorithmic_bytes_formula():
 
 def test_profile_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     srcs = ("mqo_step.cu", "mqo_step.cuh", "mqo_dev.cuh")
-    h = hashlib.sha256()
-    for f in srcs:
-        h.update(open(os.path.join(ROOT, "paper_2605_06921_gb300", "csrc", f), "rb").read())
+    h = bench.source_hash(srcs)
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "x.txt").write_text(f"source_sha256: {h.hexdigest()}\ndram_bytes_per_launch[smem]: 1.5e8\n")
+    (prof / "x.txt").write_text(f"source_sha256: {h}\ndram_bytes_per_launch[smem]: 1.5e8\n")
     (prof / "y.txt").write_text(f"source_sha256: {'0' * 64}\ndram_bytes_per_launch[smem]: 1.5e8\n")
     # read the summaries from the temporary folder, the sources from the repository
     real_join = os.path.join
@@ -43,6 +40,14 @@ def test_profile_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench.profile_traffic("y", "smem", srcs) is None      # the kernel changed since the capture
     assert bench.profile_traffic("x", "global", srcs) is None    # no figure for that variant
     assert bench.profile_traffic("missing", "smem", srcs) is None
+
+
+def test_code_text_ignores_comments_and_blanks_only():
+    a = 'int f(int x) {  // one\n  return x + 1; /* two */ }\nconst char* s = "// kept";\n'
+    b = 'int f(int x) { return x + 1; }\nconst char* s = "// kept";'
+    assert bench.code_text(a) == bench.code_text(b)
+    assert bench.code_text(a) != bench.code_text(a.replace("x + 1", "x + 2"))
+    assert '"// kept"' in bench.code_text(a)
 
 
 def test_committed_profiles_carry_traffic_for_the_current_sources():

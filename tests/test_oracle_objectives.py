@@ -1,6 +1,6 @@
-"""Pins of the oracle's four MaxCut relaxations (Sec. 3: f_L of Eq. Cut QUBO,
-f_P of Eq. perturbed Laplacian cut, f_A of Eq. adj cut formulation, f_B of
-Eq. adj_lin_two_props) against their definitions and the paper's statements
+"""Pins of the oracle's four MaxCut relaxations (Sec. 3: f_L of Eq. 4,
+f_P of Eq. 5, f_A of Eq. 6, f_B of
+Eq. 7) against their definitions and the paper's statements
 about their fixed points (Prop. 3.2, Thm 3.3, Prop. 3.4, Thm 3.6)."""
 import itertools
 

@@ -81,7 +81,7 @@ def _indep_maximal(A, z):
 
 
 def test_mis_checker_is_maximal_independent_set_exhaustive():
-    """Checker of Eq. (MIS checking) <=> maximal independent set, over all
+    """Checker of Eq. 8 <=> maximal independent set, over all
     2^n binary points of small graphs (Prop. 3.1 and its derivation)."""
     for seed in range(6):
         g = small_graph(9, 0.35, seed)
@@ -113,7 +113,7 @@ def test_mis_checker_equals_literal_pga_fixed_point():
 
 
 def test_cut_value_two_ways_and_fb_fixed_point_literal():
-    """cut = #crossing edges = f_L(s) = 1/4 s^T L s (Eq. Cut QUBO); non-fixed
+    """cut = #crossing edges = f_L(s) = 1/4 s^T L s (Eq. 4); non-fixed
     count = #coordinates moved by Pi(s + alpha grad f_B(s)) (Thm 3.6)."""
     rng = np.random.default_rng(4)
     for seed in range(4):
