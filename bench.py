@@ -7,7 +7,13 @@ graph (16,384 trajectories), BF16 x / momentum state with FP32 arithmetic.
 A step is one tick of the full per-trajectory machine over all
 trajectories (fused SpMM-gradient step, projection, rounding, exact
 evaluation, acceptance, mutation resets, repair and local search).
-Metric: edge-updates/s = nnz * B per step / step time.
+Metric: edge-updates/s = CSR entries of the member graph for every
+trajectory tick that ran a gradient step, per second of the timed ticks
+(trajectories in a repair or local-search round that tick are not counted).
+The default line carries sub-records: the steady state, batched against
+single-instance quality, the other configurations (MaxCut on a 3-regular
+graph, MIS at 10^7 nodes, the f_B autograd workload) and the paper-shaped
+ER workloads.
 
 Arms:
   default            the CUDA library (one process per GPU, weak scaling)
@@ -63,6 +69,20 @@ WORKLOADS = {
                                descent_cap=200, init_kind=1, sigma=0.1,
                                paper={"table": "Table 1 (MaxCut, 10-minute budget), (1000, 100)",
                                       "mQO-MaxCut": 28518.375, "pmQO-MaxCut": 28530.875, "Gurobi": 28534.75}),
+    # more of Table 1's ER shapes with their rows of the App. G tables
+    "er_mis_3000_100": dict(desc="MIS on 8 ER graphs (n, d) = (3000, 100), B=128 per graph", problem=0, batch=128,
+                            alpha=0.8, momentum=0.3, gamma=2.0, rho=0.6, t_gs=60, descent_cap=50, init_kind=1,
+                            sigma=0.1, paper={"table": "Table 1 (MIS, 5-minute budget), (3000, 100)",
+                                              "mQO-MIS": 198.25, "pmQO-MIS": 201.63, "ReduMIS": 201.00}),
+    "er_mis_1000_500": dict(desc="MIS on 8 ER graphs (n, d) = (1000, 500), B=128 per graph", problem=0, batch=128,
+                            alpha=0.8, momentum=0.45, gamma=2.0, rho=0.6, t_gs=60, descent_cap=50, init_kind=1,
+                            sigma=0.1, paper={"table": "Table 1 (MIS, 5-minute budget), (1000, 500)",
+                                              "mQO-MIS": 14.75, "pmQO-MIS": 14.88, "ReduMIS": 15.00}),
+    "er_maxcut_1000_500": dict(desc="MaxCut f_B on 8 ER graphs (n, d) = (1000, 500), B=128 per graph", problem=1,
+                               batch=128, alpha=0.0025, momentum=0.8, lambda_=0.001, rho=0.8, t_gs=90,
+                               descent_cap=200, init_kind=1, sigma=0.1,
+                               paper={"table": "Table 1 (MaxCut, 10-minute budget), (1000, 500)",
+                                      "mQO-MaxCut": 130997.375, "pmQO-MaxCut": 131009.125, "Gurobi": 131009.875}),
 }
 
 
@@ -81,8 +101,9 @@ def make_graph(name):
         return mi.workload_maxcut_regular(signed=True)
     if name == "mis_scale":
         return mi.workload_mis_scale()
-    if name in ("er_mis_1000_100", "er_maxcut_1000_100"):
-        return mi.workload_er_table(1000, 100.0)
+    if name.startswith("er_"):
+        n, d = (int(t) for t in name.split("_")[-2:])
+        return mi.workload_er_table(n, float(d))
     if name == "autograd_powerlaw":
         return mi.workload_chung_lu()
     raise ValueError(name)
@@ -106,11 +127,13 @@ def _oracle_job(args):
         pg = oracle.PoolGraph(og, p, traj, B)
         t0 = time.perf_counter()
         pg.run(ticks)
-        return time.perf_counter() - t0, int(rp[-1]) * ticks * B, pg.pool.best
+        dt = time.perf_counter() - t0
+        return dt, int(rp[-1]) * sum(pg.state(b)["steps"] for b in range(B)), pg.pool.best
     tr = oracle.Trajectory(og, p, traj)
     t0 = time.perf_counter()
     tr.run(ticks)
-    return time.perf_counter() - t0, int(rp[-1]) * ticks, tr.state["best"]
+    # edge-updates of the ticks that ran a gradient step
+    return time.perf_counter() - t0, int(rp[-1]) * tr.state["steps"], tr.state["best"]
 
 
 _POOLS = {}
@@ -377,13 +400,222 @@ def source_hash(sources) -> str:
 
 
 STEP_SOURCES = {"smem": ("mqo_step.cu", "mqo_step.cuh", "mqo_dev.cuh"),
-                "global": ("mqo_step_generic.cu", "mqo_step.cuh", "mqo_dev.cuh")}
+                "global": ("mqo_step_generic.cu", "mqo_step.cuh", "mqo_dev.cuh"),
+                "staged": ("mqo_step_staged.cu", "mqo_step.cuh", "mqo_dev.cuh")}
 
 
 def step_kernel_traffic(workload, x_dtype, variant):
-    """DRAM bytes per launch of the step kernel variant (smem, smem_wide, global)."""
-    src = STEP_SOURCES["global" if variant == "global" else "smem"]
+    """DRAM bytes per launch of the step kernel variant (smem, smem_wide, staged, global)."""
+    src = STEP_SOURCES[variant if variant in ("global", "staged") else "smem"]
     return profile_traffic(f"step_kernel_{workload}_{x_dtype}", variant, src)
+
+
+INT64_MIN = -(1 << 63)
+
+
+def per_graph_nnz(G):
+    off = np.asarray(G.node_offsets, dtype=np.int64)
+    return (G.row_ptr[off[1:]] - G.row_ptr[off[:-1]]).astype(np.int64)
+
+
+def best_summary(vals):
+    """Best values over the trajectories that have accepted a set (the others
+    still hold INT64_MIN) and how many have."""
+    v = np.asarray(vals, dtype=np.int64)
+    ok = v != INT64_MIN
+    return {"best_mean": float(v[ok].mean()) if ok.any() else None,
+            "best_max": int(v[ok].max()) if ok.any() else None,
+            "accepted": int(ok.sum()), "trajectories": int(v.size)}
+
+
+def solver_kwargs(wl, seed, pool_k=0, objective=0):
+    pkw = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
+                              "sigma")}
+    pkw.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), seed=seed, pool_k=pool_k,
+               objective=objective)
+    return pkw
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def measure_solver(mq, G, pkw, xd, vd, steps, warmup, *, autotune=False, clocks_of=None, barrier=None,
+                   phase_ticks=50, extra_ticks=0, probe=0):
+    """`warmup` ticks (then the autotuner), `steps` ticks timed with CUDA
+    events as a user runs them (mqo_run: replays of the captured tick
+    graphs), the per-kernel split from the next ticks (instrumented, not
+    timed), then `extra_ticks` more before the best values are read.  The
+    stepped edge-updates of the timed ticks (CSR entries of the member graph
+    for every trajectory tick that ran a gradient step) come from the
+    machine's per-trajectory step counters read before and after."""
+    import torch
+    g = mq.Graph(G)
+    s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **pkw))
+    s.run(warmup)
+    tuned = s.autotune(10) if autotune else None
+    B = pkw["batch"]
+    nnz_t = np.repeat(per_graph_nnz(G), B)
+    st0 = s.steps_taken()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    sampler = ClockSampler(clocks_of) if clocks_of is not None else None
+    if sampler:
+        sampler.__enter__()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.run(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    if sampler:
+        sampler.__exit__()
+    ms = e0.elapsed_time(e1)
+    dsteps = s.steps_taken() - st0
+    pt = min(steps, phase_ticks)
+    phase_sum, launches = s.run_timed(pt)
+    rec = {"ms": ms, "steps": steps, "phase_ms": {k: v * steps / pt for k, v in phase_sum.items()},
+           "launches": launches * steps // pt, "stepped_edge_updates": float((dsteps * nnz_t).sum()),
+           "stepped_fraction": float(dsteps.sum()) / float(steps * len(nnz_t)),
+           "all_edge_updates": float(G.nnz) * B * steps, "clocks": sampler.summary() if sampler else None,
+           "plan": s.info()}
+    if tuned:
+        rec["plan"]["autotune_ms_per_tick"] = tuned["ms_per_tick"]
+    if extra_ticks:
+        s.run(extra_ticks)
+    rec["ticks_total"] = warmup + steps + pt + extra_ticks
+    vals, _ = s.best(want_bits=False)
+    rec["vals"] = vals
+    rec.update(best_summary(vals))
+    if probe:
+        # the FP64 relaxed objective (timed on the device) and, for a few
+        # trajectories in a descent, the stored x: the CPU leg states the
+        # error of that objective against the oracle's all-double one
+        o0 = torch.cuda.Event(enable_timing=True)
+        o1 = torch.cuda.Event(enable_timing=True)
+        o0.record()
+        obj = s.objective_f64()
+        o1.record()
+        torch.cuda.synchronize()
+        x = s.get_x()
+        st = s.traj_state()
+        T = len(st)
+        samples = []
+        for t in range(0, T, max(1, T // probe)):
+            gi, b = divmod(t, B)
+            if st[t]["phase"] != 0:  # x is defined in a descent only
+                continue
+            lo, hi = int(G.node_offsets[gi]), int(G.node_offsets[gi + 1])
+            samples.append((gi, t, x[lo:hi, b].float().cpu().numpy().astype(np.float64), float(obj[t].item())))
+        rec["objective_probe"] = {"ms": o0.elapsed_time(o1), "samples": samples}
+    s.close()
+    g.close()
+    return rec
+
+
+def objective_error(G, wl, objective, probe):
+    """Largest relative error of the device's FP64 relaxed objective ((Ax)_v
+    accumulated in float32, the rest in double) against the oracle's
+    all-double objective of the same stored x, over the probed trajectories."""
+    import oracle
+    errs = []
+    for gi, t, xs, got in probe.get("samples", []):
+        og = oracle.Graph(G.subgraph(gi) if G.num_graphs > 1 else G)
+        if wl["problem"] == 0:
+            want = oracle.objective_f64(og, 0, wl.get("gamma", 2.0), 0.0, xs)
+        else:
+            want = oracle.cut_objective_f64(og, objective, wl.get("lambda_", 0.001), xs)
+        errs.append(abs(got - want) / max(abs(want), 1e-30))
+    return {"device_ms": probe.get("ms"), "trajectories_checked": len(errs),
+            "max_rel_error_vs_fp64_oracle": max(errs) if errs else None}
+
+
+def oracle_single(G, wl, xd, vd, ticks, objective=0):
+    """One trajectory of member graph 0, `ticks` ticks, on one host core in
+    this process (graphs too large to ship to a process pool)."""
+    pd = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
+                             "sigma") if k in wl}
+    pd.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), x_dtype=xd, v_dtype=vd, seed=0,
+              pool_k=0, objective=objective)
+    sub = G.subgraph(0) if G.num_graphs > 1 else G
+    dt, eu, _ = _oracle_job((0, sub.row_ptr, sub.col_idx, sub.weights, sub.n, pd, 0, ticks))
+    return dict(value=eu / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"one trajectory of member graph 0 (n={sub.n}, nnz={sub.nnz}) for {ticks} ticks on one "
+                       f"core, {eu:.3e} stepped edge-updates in {dt:.2f} s")
+
+
+STEP_KERNEL_NAMES = {"smem": "mqo::k_step_s", "smem_wide": "mqo::k_step_s", "staged": "mqo::k_step_q",
+                     "global": "mqo::k_step_g"}
+
+
+def step_roofline(G, B, sx, sv, step_ms, plan, workload, x_dtype, hbm_peak, peak_src, clocks, n_sm, peaks):
+    """Roofline of the step kernel: algorithmic HBM bytes (CSR once, x and V
+    read and written once, rounding words) per launch over its average
+    launch time; the shared-memory kernel adds its gather bound."""
+    alg = algorithmic_bytes_per_step(G, B, sx, sv)
+    achieved = alg / (step_ms / 1e3) / 1e9
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+           "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+    kern = plan["step_kernel"]
+    traffic = step_kernel_traffic(workload, x_dtype, kern)
+    gathered = float(G.nnz) * B * sx  # neighbour rows of x read per launch
+    if kern.startswith("smem"):
+        sm_clock = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+        smem_peak = 128.0 * n_sm * sm_clock * 1e6 / 1e9
+        smem_achieved = gathered / (step_ms / 1e3) / 1e9
+        roof = {"bound": "smem", "achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": smem_achieved / smem_peak, "traffic": traffic,
+                "peak_derivation": f"128 B/clk/SM x {n_sm} SMs x {sm_clock:.0f} MHz (sampled SM clock)",
+                "algorithmic_bytes_per_launch": gathered, "hbm": hbm}
+    else:
+        # the neighbour-row gathers are requests to L2; the share that misses
+        # is DRAM traffic on top of the algorithmic bytes (measured: traffic)
+        roof = dict(hbm, traffic=traffic, gathered_bytes_per_launch=gathered,
+                    achieved_incl_gathers=(alg + gathered) / (step_ms / 1e3) / 1e9)
+    roof.update(kernel=STEP_KERNEL_NAMES.get(kern, kern), step_kernel_ms=step_ms, plan=plan)
+    return roof
+
+
+def solver_config_record(mq, name, xd_s, vd_s, steps, warmup, extra_ticks, *, local, rank, cpu, G=None,
+                         objective="fb", oracle_ticks=20):
+    """Sub-record of the default bench line for another solver workload:
+    throughput (stepped edge-updates/s), its step kernel's roofline, best
+    values after a fixed tick budget, the FP64 objective error and (rank 0)
+    a single-core oracle slice."""
+    import torch
+    wl = WORKLOADS[name]
+    G = make_graph(name) if G is None else G
+    B = wl["batch"]
+    xd, vd = dtype_code(xd_s), dtype_code(vd_s)
+    sx, sv = (4 if xd == 0 else 2), (4 if vd == 0 else 2)
+    pkw = solver_kwargs(wl, 1000 * rank, 0, OBJECTIVES[objective])
+    r = measure_solver(mq, G, pkw, xd, vd, steps, warmup, autotune=True, clocks_of=local, extra_ticks=extra_ticks,
+                       probe=4 if cpu else 0)
+    peaks = read_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    step_ms = r["phase_ms"]["step"] / steps
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = step_roofline(G, B, sx, sv, step_ms, r["plan"], name, xd_s, hbm_peak,
+                         "measured" if "hbm_gbs" in peaks else "fallback", r["clocks"], n_sm, peaks)
+    rec = {"workload": wl["desc"], "x_dtype": xd_s, "v_dtype": vd_s, "dtype": f"f32 arithmetic, x {xd_s} / V {vd_s} "
+           "storage, int64 evaluation", "nodes": G.n, "nnz": G.nnz, "batch": B, "steps": steps, "warmup": warmup,
+           "value": r["stepped_edge_updates"] / (r["ms"] / 1e3), "unit": UNIT,
+           "value_all_trajectories": r["all_edge_updates"] / (r["ms"] / 1e3),
+           "stepped_fraction": r["stepped_fraction"], "ms_per_step": r["ms"] / steps,
+           "kernel_ms_per_step": {k: v / steps for k, v in r["phase_ms"].items()}, "roofline": roof,
+           "clocks": r["clocks"], "gpu_launches": r["launches"], "best_after_ticks": r["ticks_total"]}
+    rec.update({k: r[k] for k in ("best_mean", "best_max", "accepted", "trajectories")})
+    if cpu:
+        rec["objective_f64"] = objective_error(G, wl, OBJECTIVES[objective], r.get("objective_probe", {}))
+        rec["cpu_baseline"] = oracle_single(G, wl, xd, vd, oracle_ticks, OBJECTIVES[objective])
+    return rec
 
 
 def gpu_arm(args):
@@ -408,121 +640,24 @@ def gpu_arm(args):
     sx, sv = (4 if xd == 0 else 2), (4 if vd == 0 else 2)
     G = make_graph(args.workload)
     B = wl["batch"]
-    pkw = {k: wl[k] for k in ("problem", "batch", "alpha", "momentum", "rho", "t_gs", "descent_cap", "init_kind",
-                              "sigma")}
-    pkw.update(gamma=wl.get("gamma", 2.0), lambda_=wl.get("lambda_", 0.001), seed=1000 * rank,
-               pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
+    pkw = solver_kwargs(wl, 1000 * rank, args.pool_k, OBJECTIVES[args.objective])
+    peaks = read_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu
 
-    info_launches = [0]
-    objective_probe = {}
-
-    def measure(x_dtype, v_dtype, steps, warmup, sample_clocks, autotune=False):
-        g = mq.Graph(G)
-        s = mq.Solver(g, mq.params(x_dtype=x_dtype, v_dtype=v_dtype, **pkw))
-        s.run(warmup)
-        tuned = s.autotune(10) if autotune else None
-        torch.cuda.synchronize()
-        barrier()
-        sampler = ClockSampler(local) if sample_clocks else None
-        if sampler:
-            sampler.__enter__()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        s.run(steps)  # the captured tick graphs, as a user runs them
-        e1.record()
-        torch.cuda.synchronize()
-        barrier()
-        if sampler:
-            sampler.__exit__()
-        ms = e0.elapsed_time(e1)
-        clocks = sampler.summary() if sampler else None
-        # per-kernel breakdown: the next ticks again, captured with an event
-        # node between consecutive kernels (the events add time of their own,
-        # so these are not the timed region)
-        phase_ticks = min(steps, 50)
-        phase_sum, launches = s.run_timed(phase_ticks)
-        phase_ms = {k: v * steps / phase_ticks for k, v in phase_sum.items()}
-        info_launches[0] = launches * steps // phase_ticks
-        vals, _ = s.best(want_bits=False)
-        info = s.info()
-        if tuned:
-            info["autotune_ms_per_tick"] = tuned["ms_per_tick"]
-        if sample_clocks:
-            # the FP64 relaxed objective of the final iterate (timed on the
-            # device) and, for a few sampled trajectories, the stored x, so
-            # that the cpu_baseline leg can state its error against the oracle
-            o0 = torch.cuda.Event(enable_timing=True)
-            o1 = torch.cuda.Event(enable_timing=True)
-            o0.record()
-            obj = s.objective_f64()
-            o1.record()
-            torch.cuda.synchronize()
-            x = s.get_x()
-            st = s.traj_state()
-            objective_probe["ms"] = o0.elapsed_time(o1)
-            objective_probe["samples"] = []
-            for t in range(0, G.num_graphs * B, max(1, (G.num_graphs * B) // 8)):
-                gi, b = divmod(t, B)
-                if st[t]["phase"] != 0:  # x is defined in a descent only
-                    continue
-                lo, hi = int(G.node_offsets[gi]) if G.node_offsets is not None else 0, \
-                    int(G.node_offsets[gi + 1]) if G.node_offsets is not None else G.n
-                objective_probe["samples"].append((gi, t, x[lo:hi, b].float().cpu().numpy().astype(np.float64),
-                                                   float(obj[t].item())))
-        s.close()
-        g.close()
-        return ms, phase_ms, clocks, vals, info
-
-    nnz_b = G.nnz * B
-    ms, phase_ms, clocks, best_vals, plan = measure(xd, vd, args.steps, args.warmup, True, not args.no_autotune)
-    timed_launches = info_launches[0]
-    step_avg_ms = phase_ms["step"] / args.steps
-    ms, value = aggregate_ranks(ms, float(nnz_b) * args.steps, dist, "cuda")
-
-    # the plain FP32-state form of the same workload, for comparison
-    f32 = None
-    single = None
-    if xd != 0 and not args.no_compare:
-        k32 = args.steps
-        ms32, ph32, _, vals32, _ = measure(0, 0, k32, args.warmup, False)
-        f32 = {"value": nnz_b * k32 / (ms32 / 1e3), "ms_per_step": ms32 / k32, "step_kernel_ms": ph32["step"] / k32,
-               "best_mean": float(np.mean(vals32)), "best_max": int(np.max(vals32)), "ticks": args.warmup + k32}
-        if G.num_graphs > 1:
-            # the plain form: member graph 0 alone, FP32 state, the same B
-            # trajectories (keyed by graph and slot, so identical to the
-            # batch's first B) and the same number of ticks
-            G0 = G.subgraph(0)
-            g0 = mq.Graph(G0)
-            s0 = mq.Solver(g0, mq.params(x_dtype=0, v_dtype=0, **pkw))
-            s0.run(args.warmup)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            s0.run(args.steps)
-            e1.record()
-            torch.cuda.synchronize()
-            ms0 = e0.elapsed_time(e1)
-            vals0, _ = s0.best(want_bits=False)
-            s0.close()
-            g0.close()
-            single = {"value": G0.nnz * B * args.steps / (ms0 / 1e3), "unit": UNIT, "ms_per_step": ms0 / args.steps,
-                      "graph": f"member graph 0 alone (n={G0.n}, nnz={G0.nnz}), B={B}, f32 state",
-                      "best_mean": float(np.mean(vals0)), "batched_bf16_best_mean_same_graph": float(np.mean(best_vals[:B])),
-                      "batched_f32_best_mean_same_graph": float(np.mean(vals32[:B])), "ticks": args.warmup + args.steps}
+    main = measure_solver(mq, G, pkw, xd, vd, args.steps, args.warmup, autotune=not args.no_autotune,
+                          clocks_of=local, barrier=barrier, probe=8 if cpu_leg else 0)
+    ms, value = aggregate_ranks(main["ms"], main["stepped_edge_updates"], dist, "cuda")
+    _, value_all = aggregate_ranks(main["ms"], main["all_edge_updates"], dist, "cuda")
+    step_avg_ms = main["phase_ms"]["step"] / args.steps
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = step_roofline(G, B, sx, sv, step_avg_ms, main["plan"], args.workload, args.x_dtype, hbm_peak, peak_src,
+                         main["clocks"], n_sm, peaks)
 
     # end to end through the public API with host buffers: graph upload from
-    # pinned host arrays (validated on the host), solver creation, every tick
-    # followed by a device->host read of the per-trajectory best values
+    # pinned host arrays, solver creation, every tick followed by a
+    # device->host read of the per-trajectory best values
     def pinned(a):
         return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
 
@@ -540,18 +675,20 @@ def gpu_arm(args):
     e2e_steps = args.steps
     for _ in range(e2e_steps):
         s.run(1)
-        vals, _ = s.best(want_bits=False)
+        s.best(want_bits=False)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
-    t_e2e = t3 - t0
+    e2e_stepped = float((s.steps_taken() * np.repeat(per_graph_nnz(G), B)).sum())
     s.close()
     g.close()
-    ms_e2e, e2e_value = aggregate_ranks(t_e2e * 1e3, float(nnz_b) * e2e_steps, dist, "cuda")
+    ms_e2e, e2e_value = aggregate_ranks((t3 - t0) * 1e3, e2e_stepped, dist, "cuda")
     csr_bytes = G.nnz * 4 + (G.n + 1) * 8 + (G.nnz if G.weights is not None else 0) + 8 * (G.num_graphs + 1)
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(csr_bytes / e2e_steps), "d2h_bytes_per_step": int(8 * G.num_graphs * B),
            "graph_upload_ms": (t1 - t0) * 1e3, "solver_create_ms": (t2 - t1) * 1e3,
-           "ticks_ms": (t3 - t2) * 1e3, "steps": e2e_steps}
+           "ticks_ms": (t3 - t2) * 1e3, "steps": e2e_steps,
+           "note": "stepped edge-updates of the ticks run from a fresh start, graph upload and solver creation "
+                   "inside the timed region"}
 
     alg = algorithmic_bytes_per_step(G, B, sx, sv)
     if alg > L2_BYTES:
@@ -559,103 +696,328 @@ def gpu_arm(args):
     else:
         l2_note = (f"CSR + state touched per step {alg / 1e6:.0f} MB fit in the 126 MB L2 and stay resident between "
                    f"ticks by design (not flushed)")
-    hbm_achieved = alg / (step_avg_ms / 1e3) / 1e9
-    hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-           "frac": hbm_achieved / hbm_peak, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
-    traffic = step_kernel_traffic(args.workload, args.x_dtype, plan["step_kernel"])
-    if plan["step_kernel"].startswith("smem"):
-        # every neighbour row of x is read from shared memory once per step:
-        # nnz * B * sx bytes; peak = one 128-byte wavefront per clock per SM
-        sm_clock = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
-        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        smem_peak = 128.0 * n_sm * sm_clock * 1e6 / 1e9
-        gathered = float(G.nnz) * B * sx
-        smem_achieved = gathered / (step_avg_ms / 1e3) / 1e9
-        roof = {"bound": "smem", "achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
-                "frac": smem_achieved / smem_peak, "traffic": traffic,
-                "peak_derivation": f"128 B/clk/SM x {n_sm} SMs x {sm_clock:.0f} MHz (sampled SM clock)",
-                "algorithmic_bytes_per_launch": gathered, "hbm": hbm}
-    else:
-        roof = dict(hbm, traffic=traffic)
-    roof.update(kernel="mqo::k_step_s" if plan["step_kernel"].startswith("smem") else "mqo::k_step_g",
-                step_kernel_ms=step_avg_ms, plan=plan)
 
     # quality on the paper-shaped workloads: best value per member graph (max
     # over its trajectories) after a longer tick budget, without and with a pool
-    quality = None
-    if "paper" in wl and args.quality_ticks > 0:
-        quality = {"ticks": args.quality_ticks, "paper": wl["paper"],
-                   "note": "paper: its own 8 ER graphs, time budget on its hardware; here: seeded synthetic "
-                           "ER graphs of the same (n, d), tick budget -- context, not a like-for-like comparison"}
-        for label, k in (("independent", 0), ("pool_k8", 8)):
-            qkw = dict(pkw, pool_k=k)
-            g = mq.Graph(G)
-            s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **qkw))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s.run(args.quality_ticks)
-            vals, _ = s.best(want_bits=False)
-            dt = time.perf_counter() - t0
-            per_graph = vals.reshape(G.num_graphs, B).max(axis=1)
-            quality[label] = {"best_per_graph_mean": float(per_graph.mean()), "best_per_graph": per_graph.tolist(),
-                              "seconds": dt}
-            # gains breakdown of each graph's best trajectory (first descent,
-            # then the increases from resets / restarts and from local search)
-            sts = s.traj_state()
-            pick = vals.reshape(G.num_graphs, B).argmax(axis=1)
-            br = [sts[gi * B + int(pick[gi])] for gi in range(G.num_graphs)]
-            quality[label]["breakdown_mean"] = {
-                "first_descent": float(np.mean([x["first_value"] for x in br])),
-                "gain_resets": float(np.mean([x["gain_descent"] for x in br])),
-                "gain_local_search": float(np.mean([x["gain_ls"] for x in br]))}
-            s.close()
-            g.close()
+    quality = paper_quality(mq, G, wl, pkw, xd, vd, args.quality_ticks) if "paper" in wl and args.quality_ticks > 0 \
+        else None
+
+    sub = {}
+    if args.workload == "mis_batched" and not args.no_sub and world == 1 and args.pool_k == 0:
+        sub = default_line_subrecords(mq, G, wl, pkw, xd, vd, args.x_dtype, local=local, rank=rank, cpu=cpu_leg)
 
     cpu = None
     objective_f64 = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if cpu_leg:
         cpu = oracle_sample(G, wl, xd, vd, target_s=12.0, pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
-        # error of the device's FP64 relaxed objective ((Ax)_v accumulated in
-        # float32) against the oracle's all-double objective of the same x
-        import oracle
-        errs = []
-        for gi, t, xs, got in objective_probe.get("samples", []):
-            og = oracle.Graph(G.subgraph(gi) if G.num_graphs > 1 else G)
-            if wl["problem"] == 0:
-                want = oracle.objective_f64(og, 0, wl.get("gamma", 2.0), 0.0, xs)
-            else:
-                want = oracle.cut_objective_f64(og, OBJECTIVES[args.objective], wl.get("lambda_", 0.001), xs)
-            errs.append(abs(got - want) / max(abs(want), 1e-30))
-        objective_f64 = {"device_ms": objective_probe.get("ms"), "trajectories_checked": len(errs),
-                         "max_rel_error_vs_fp64_oracle": max(errs) if errs else None}
+        objective_f64 = objective_error(G, wl, OBJECTIVES[args.objective], main.get("objective_probe", {}))
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": f"f32 (x {args.x_dtype} / V {args.v_dtype or args.x_dtype} storage, int64 evaluation)",
+            "data": "synthetic",
             "config": {"workload": wl["desc"], "x_dtype": args.x_dtype, "v_dtype": args.v_dtype or args.x_dtype,
-                       "nnz": G.nnz, "nodes": G.n, "batch": B, "edge_updates_per_step": nnz_b,
+                       "nnz": G.nnz, "nodes": G.n, "batch": B, "edge_updates_per_step": G.nnz * B,
+                       "value_counts": "CSR entries of the member graph for every trajectory tick that ran a "
+                                       "gradient step (stepped_fraction of all trajectory ticks)",
                        "l2": l2_note, "parallelism": f"replicas x{world}",
                        "pool_k": args.pool_k, "objective": args.objective},
-            "roofline": roof, "e2e": e2e, "gpu_launches": timed_launches,
-            "kernel_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-            "clocks": clocks, "best_mean": float(np.mean(best_vals)), "best_max": int(np.max(best_vals)),
+            "value_all_trajectories": value_all, "stepped_fraction": main["stepped_fraction"],
+            "roofline": roof, "e2e": e2e, "gpu_launches": main["launches"],
+            "kernel_ms_per_step": {k: v / args.steps for k, v in main["phase_ms"].items()},
+            "clocks": main["clocks"],
         }
-        if f32:
-            line["fp32_state"] = f32
-        if single:
-            line["single_instance_fp32"] = single
+        line.update({k: main[k] for k in ("best_mean", "best_max", "accepted", "trajectories")})
+        line["best_after_ticks"] = main["ticks_total"]
         if cpu:
             line["cpu_baseline"] = cpu
         if quality:
             line["quality"] = quality
         if objective_f64:
             line["objective_f64"] = objective_f64
+        line.update(sub)
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def paper_quality(mq, G, wl, pkw, xd, vd, ticks):
+    """Best value per member graph (max over its trajectories) after `ticks`
+    ticks, independent trajectories and a pool of 8, with the gains
+    breakdown of each graph's best trajectory."""
+    import torch
+    B = wl["batch"]
+    quality = {"ticks": ticks, "paper": wl["paper"],
+               "note": "paper: its own ER graphs, time budget on its hardware; here: seeded synthetic ER graphs of "
+                       "the same (n, d), tick budget -- context, not a like-for-like comparison"}
+    for label, k in (("independent", 0), ("pool_k8", 8)):
+        g = mq.Graph(G)
+        s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **dict(pkw, pool_k=k)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.run(ticks)
+        vals, _ = s.best(want_bits=False)
+        dt = time.perf_counter() - t0
+        per_graph = vals.reshape(G.num_graphs, B).max(axis=1)
+        quality[label] = {"best_per_graph_mean": float(per_graph.mean()), "best_per_graph": per_graph.tolist(),
+                          "seconds": dt}
+        sts = s.traj_state()
+        pick = vals.reshape(G.num_graphs, B).argmax(axis=1)
+        br = [sts[gi * B + int(pick[gi])] for gi in range(G.num_graphs)]
+        quality[label]["breakdown_mean"] = {
+            "first_descent": float(np.mean([x["first_value"] for x in br])),
+            "gain_resets": float(np.mean([x["gain_descent"] for x in br])),
+            "gain_local_search": float(np.mean([x["gain_ls"] for x in br]))}
+        s.close()
+        g.close()
+    return quality
+
+
+def steady_state(mq, G, pkw, xd, vd, *, warm, repeats, ticks, local):
+    """The workload after `warm` ticks (every trajectory past its first
+    descents), `repeats` timed windows of `ticks` ticks: median, min and max
+    of the stepped edge-updates/s."""
+    import torch
+    B = pkw["batch"]
+    g = mq.Graph(G)
+    s = mq.Solver(g, mq.params(x_dtype=xd, v_dtype=vd, **pkw))
+    s.run(warm)
+    s.autotune(10)
+    nnz_t = np.repeat(per_graph_nnz(G), B)
+    vals, fracs, mss = [], [], []
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    for _ in range(repeats):
+        st0 = s.steps_taken()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.run(ticks)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        d = s.steps_taken() - st0
+        vals.append(float((d * nnz_t).sum()) / (ms / 1e3))
+        fracs.append(float(d.sum()) / float(ticks * len(nnz_t)))
+        mss.append(ms / ticks)
+    sampler.__exit__()
+    best = best_summary(s.best(want_bits=False)[0])
+    s.close()
+    g.close()
+    return {"warmup_ticks": warm, "repeats": repeats, "ticks_per_repeat": ticks,
+            "value_median": statistics.median(vals), "value_min": min(vals), "value_max": max(vals), "unit": UNIT,
+            "ms_per_step_median": statistics.median(mss), "stepped_fraction_median": statistics.median(fracs),
+            "clocks": sampler.summary(), "best_mean": best["best_mean"], "accepted": best["accepted"]}
+
+
+def quality_vs_single(mq, G, pkw, xd, vd, xname, *, ticks):
+    """The batched form (all member graphs in one launch, the workload's
+    storage type), the same batch in FP32, and member graph 0 alone in FP32
+    (the plain single-instance form) for the same tick budget: stepped
+    edge-updates/s, and the best values of member graph 0's B trajectories
+    (keyed by graph and slot, so the three runs start from the same points)."""
+    import torch
+    B = pkw["batch"]
+    out = {"ticks": ticks, "graph": "member graph 0 of the batch"}
+    for label, gg, x_d, v_d in ((f"batched_{xname}", G, xd, vd), ("batched_f32", G, 0, 0),
+                                ("single_instance_f32", G.subgraph(0), 0, 0)):
+        g = mq.Graph(gg)
+        s = mq.Solver(g, mq.params(x_dtype=x_d, v_dtype=v_d, **pkw))
+        s.run(10)
+        nnz_t = np.repeat(per_graph_nnz(gg), B)
+        st0 = s.steps_taken()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.run(ticks - 10)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        d = s.steps_taken() - st0
+        vals, _ = s.best(want_bits=False)
+        out[label] = {"value": float((d * nnz_t).sum()) / (ms / 1e3), "unit": UNIT,
+                      "ms_per_step": ms / (ticks - 10), "graph0": best_summary(vals[:B])}
+        s.close()
+        g.close()
+    return out
+
+
+PAPER_ER = ("er_mis_1000_100", "er_maxcut_1000_100", "er_mis_3000_100", "er_mis_1000_500", "er_maxcut_1000_500")
+
+
+def paper_er_record(mq, ticks, rank):
+    """Best value per graph (max over its B trajectories, mean over the 8
+    seeded graphs) after `ticks` ticks on the paper-shaped ER workloads,
+    independent trajectories, next to the paper's Table 1 numbers."""
+    import torch
+    out = {"ticks": ticks, "note": "seeded synthetic ER graphs of the paper's (n, d), tick budget; the paper's "
+                                   "numbers come from its own graphs and a time budget: context only"}
+    for name in PAPER_ER:
+        wl = WORKLOADS[name]
+        G = make_graph(name)
+        B = wl["batch"]
+        g = mq.Graph(G)
+        s = mq.Solver(g, mq.params(x_dtype=1, v_dtype=1, **solver_kwargs(wl, 1000 * rank)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.run(ticks)
+        vals, _ = s.best(want_bits=False)
+        dt = time.perf_counter() - t0
+        per_graph = vals.reshape(G.num_graphs, B).max(axis=1)
+        out[name] = {"best_per_graph_mean": float(per_graph.mean()), "best_per_graph": per_graph.tolist(),
+                     "seconds": dt, "ms_per_step": dt * 1e3 / ticks, "plan": s.info()["step_kernel"],
+                     "paper": wl["paper"]}
+        s.close()
+        g.close()
+    return out
+
+
+def default_line_subrecords(mq, G, wl, pkw, xd, vd, xname, *, local, rank, cpu):
+    """Sub-records of the default bench line: steady state, batched against
+    single instance, the other configurations (large MIS, MaxCut, autograd)
+    and the paper-shaped ER workloads."""
+    out = {"steady_state": steady_state(mq, G, pkw, xd, vd, warm=400, repeats=10, ticks=100, local=local),
+           "quality_vs_single_instance": quality_vs_single(mq, G, pkw, xd, vd, xname, ticks=1000)}
+    cfg = {}
+    for name, xs, vs in (("maxcut_regular", "bf16", "bf16"), ("maxcut_regular", "bf16", "f32"),
+                         ("maxcut_regular_signed", "bf16", "bf16")):
+        cfg[f"{name}_{xs}_v{vs}"] = solver_config_record(mq, name, xs, vs, 20, 5, 2000, local=local, rank=rank,
+                                                         cpu=cpu, oracle_ticks=400)
+    Gs = make_graph("mis_scale")
+    for xs in ("f16", "f32"):
+        cfg[f"mis_scale_{xs}"] = solver_config_record(mq, "mis_scale", xs, xs, 20, 5, 100, local=local, rank=rank,
+                                                      cpu=cpu and xs == "f16", G=Gs, oracle_ticks=2)
+    del Gs
+    cfg["autograd_powerlaw_f32"] = autograd_measure(mq, 20, 5, local=local, rank=rank, dist=None,
+                                                    cpu=cpu, cpu_target_s=6.0)
+    out["configs"] = cfg
+    out["paper_er"] = paper_er_record(mq, 5000, rank)
+    out["app_b"] = app_b_record(mq, rank, cpu)
+    return out
+
+
+# ---------------------------------------------------------------- App. B: the MaxCut relaxations compared
+APP_B_OBJS = ("fl", "fp", "fa", "fb")
+APP_B_TABLE5 = {(100, 50): (0.0025, 0.9), (1000, 100): (0.0025, 0.8), (1000, 500): (0.0025, 0.8),
+                (1000, 800): (0.0025, 0.8)}  # (n, d): (alpha, momentum), the App. G MaxCut rows
+
+
+def _descend(mq, G, obj, x0, alpha, momentum, steps, seed):
+    """Plain projected (momentum) ascent steps of one relaxation from x0 on
+    every trajectory: cut of the rounded start and end point, nodes that a
+    step would still move at the end (0: a fixed binary point)."""
+    import torch
+    B = x0.shape[1]
+    s = mq.Solver(mq.Graph(G), mq.params(problem=1, batch=B, alpha=alpha, momentum=momentum, lambda_=0.001,
+                                         objective=OBJECTIVES[obj], init_kind=0, seed=seed))
+    s.set_x(torch.from_numpy(x0).cuda())
+    cut0 = s.evaluate(s.round())[0].cpu().numpy()
+    s.step(steps)
+    v, a, _ = s.evaluate(s.round())
+    torch.cuda.synchronize()
+    out = (cut0, v.cpu().numpy(), a.cpu().numpy(), s.get_x().float().cpu().numpy())
+    s.close()
+    return out
+
+
+def _per_graph_mean(vals, num_graphs, B):
+    return vals.reshape(num_graphs, B).mean(axis=1)
+
+
+def app_b_record(mq, rank, cpu, steps=2000):
+    """The paper's comparison of its MaxCut relaxations (App. B): escapes from
+    f_L-interior stationary points x = c1 (Table 3) and from 1-flip
+    repairable binary points (Table 4) on 10 ER(100, 0.66) graphs, alpha 0.1,
+    lambda 0.001, plain projected gradient ascent, no local search or reset;
+    and the four relaxations from one shared random start on ER graphs of
+    the paper's (n, d) (Table 5, 3 graphs each, the App. G step sizes).
+    Cuts are exact integers of the rounded points."""
+    import torch
+    B = 32
+    out = {"note": "seeded synthetic ER graphs, not the paper's; the paper's numbers are context",
+           "steps": steps}
+    torch.cuda.synchronize()
+    tables = {}
+    replay = []
+    # the stated density p = 0.66, and p = 0.017, whose random cut (about
+    # m/2 = 42) matches the cut at initialisation that Table 4 prints
+    for dens in (0.66, 0.017):
+        G = mi.pack([mi.erdos_renyi(100, dens, 500 + k) for k in range(10)])
+        rng = np.random.default_rng(1000 * rank + 3)
+        c = rng.uniform(-1.0, 1.0, size=(G.num_graphs, B)).astype(np.float32)
+        x_c = np.repeat(c, 100, axis=0)  # x = c 1 on each graph, one c per trajectory
+        x_pm = np.where(rng.random((G.n, B)) < 0.5, -1.0, 1.0).astype(np.float32)
+        for label, x0, paper in (("table3_stationary_c1", x_c, {"fl": [0, 0], "fp": [0, 47.2], "fb": [0, 51.1]}),
+                                 ("table4_one_flip_repairable", x_pm,
+                                  {"fl": [42.4, 42.4], "fp": [42.4, 42.4], "fb": [42.4, 50.1]})):
+            t = {"paper_cut_init_and_end": paper, "graphs": f"10 ER(100, {dens})"}
+            for obj in ("fl", "fp", "fb"):
+                cut0, cut1, moving, _ = _descend(mq, G, obj, x0, 0.1, 0.0, steps, 7)
+                rec = {"cut_init_mean": float(cut0.mean()), "cut_end_mean": float(cut1.mean()),
+                       "increase_mean": float((cut1 - cut0).mean()),
+                       "escaped_fraction": float((cut1 > cut0).mean()),
+                       "still_moving_fraction": float((moving > 0).mean())}
+                if label.startswith("table4"):
+                    # the starts must be 1-flip repairable (a node with a positive gain)
+                    pos = mq.Solver(mq.Graph(G), mq.params(problem=1, batch=B, objective=OBJECTIVES[obj]))
+                    pos.set_x(torch.from_numpy(x0).cuda())
+                    rec["starts_one_flip_repairable"] = float((pos.evaluate(pos.round())[2].cpu().numpy() > 0).mean())
+                    pos.close()
+                t[obj] = rec
+                replay.append((G, obj, x0, 0.1, 0.0, cut1, steps))
+            tables[f"{label}_p{dens}"] = t
+    rng = np.random.default_rng(1000 * rank + 5)
+    t5 = {"paper_cut_mean": {"fl": [1256.2, 25298.11, 125046.6, 200030.6], "fp": [1257, 25319.95, 125021.3, 200004.7],
+                             "fa": [1397.16, 28157.02, 130331.9, 204291.2],
+                             "fb": [1397.45, 28166.59, 130336.5, 204296.5]},
+          "paper_columns": ["(100,50)", "(1000,100)", "(1000,500)", "(1000,800)"], "steps": 3 * steps}
+    for (n, d), (alpha, mom) in APP_B_TABLE5.items():
+        Gt = mi.pack([mi.erdos_renyi(n, d / n, 700 + k) for k in range(3)])
+        x0 = rng.uniform(-1.0, 1.0, size=(Gt.n, B)).astype(np.float32)
+        row = {}
+        for obj in APP_B_OBJS:
+            cut0, cut1, moving, _ = _descend(mq, Gt, obj, x0, alpha, mom, 3 * steps, 7)
+            row[obj] = {"cut_mean": float(cut1.mean()), "best_per_graph_mean":
+                        float(cut1.reshape(3, B).max(axis=1).mean()), "still_moving_fraction":
+                        float((moving > 0).mean())}
+            if n == 100:
+                replay.append((Gt, obj, x0, alpha, mom, cut1, 3 * steps))
+        t5[f"({n},{d})"] = row
+    tables["table5_relaxations"] = t5
+    out.update(tables)
+    if cpu:
+        out["oracle_replay"] = app_b_replay(replay)
+    return out
+
+
+def app_b_replay(replay):
+    """The oracle takes the same plain steps from the same start for the
+    first trajectory of the first two graphs of every Table 3/4 run and of
+    the (100, 50) row of Table 5; the rounded end cuts must be equal."""
+    import oracle
+    checked = mismatched = 0
+    for G, obj, x0, alpha, mom, cut1, nsteps in replay:
+        B = x0.shape[1]
+        p = oracle.params(problem=oracle.MAXCUT, batch=B, alpha=alpha, momentum=mom, lambda_=0.001,
+                          objective=OBJECTIVES[obj], init_kind=0)
+        for gi in range(min(G.num_graphs, 2)):
+            og = oracle.Graph(G.subgraph(gi))
+            lo, hi = int(G.node_offsets[gi]), int(G.node_offsets[gi + 1])
+            x = x0[lo:hi, 0].copy()
+            V = np.zeros_like(x)
+            for _ in range(nsteps):
+                x, V, _, _ = oracle.descent_step(og, p, x, V)
+            z = (x > 0).astype(np.uint8)
+            want = oracle.eval_cut(og, z)[0]
+            checked += 1
+            mismatched += int(want != int(cut1[gi * B]))
+    return {"trajectories": checked, "mismatched_end_cuts": mismatched}
 
 
 def fb_kernel_bytes(G, B, writes_grad):
@@ -695,17 +1057,10 @@ def _autograd_job(args):
     return c
 
 
-def autograd_arm(args):
+def autograd_measure(mq, steps, warmup, *, local, rank, dist, cpu, cpu_target_s=12.0):
+    """The f_B autograd workload: FbObjective forward + fused SpMM backward +
+    the projected momentum kernel per step; returns its bench record."""
     import torch
-    import paper_2605_06921_gb300 as mq
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     wl = AUTOGRAD
     G = make_graph("autograd_powerlaw")
     B, lam = wl["batch"], wl["lambda_"]
@@ -713,7 +1068,7 @@ def autograd_arm(args):
     gen = torch.Generator(device="cuda").manual_seed(1000 * rank)
     X = (torch.rand((G.n, B), device="cuda", generator=gen) * 2 - 1).requires_grad_(True)
     opt = mq.PGAMomentum([X], lr=wl["lr"], momentum=wl["momentum"])
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     ph = {"forward": 0.0, "backward": 0.0, "optimizer": 0.0}
 
     def step(ev=None):
@@ -731,22 +1086,18 @@ def autograd_arm(args):
             ev[3].record()
         return obj
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
+    peaks = read_peaks()
     sampler = ClockSampler(local)
     sampler.__enter__()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for k in range(args.steps):
+    for k in range(steps):
         step(evs[k])
     e1.record()
     torch.cuda.synchronize()
@@ -760,14 +1111,14 @@ def autograd_arm(args):
     clocks = sampler.summary()
     ms_total = e0.elapsed_time(e1)
     eu_step = 2.0 * G.nnz * B
-    ms, value = aggregate_ranks(ms_total, eu_step * args.steps, dist, "cuda")
+    ms, value = aggregate_ranks(ms_total, eu_step * steps, dist, "cuda")
     # forward and backward: one launch for rows of <= 512 entries and row
     # chunks, one more if some row is longer; the momentum step: one
     per_fb = 1 + int(G.degrees().max() > 512)
     launches_per_step = 2 * per_fb + 1
     # the forward launch (f_B per column: one SpMM pass, X read once); the
-    # backward is the same pass plus the gradient write and takes as long
-    fwd_ms = ph["forward"] / args.steps
+    # backward is the same pass plus the gradient write
+    fwd_ms = ph["forward"] / steps
     alg = fb_kernel_bytes(G, B, False)
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg / (fwd_ms / 1e3) / 1e9
@@ -775,7 +1126,8 @@ def autograd_arm(args):
             "traffic": profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_units", ("mqo_grad.cu", "mqo_dev.cuh")),
             "kernel": "mqo::k_fb_units (f_B forward; the fused SpMM backward is the same pass plus a write)",
             "algorithmic_bytes_per_launch": alg, "forward_ms": fwd_ms,
-            "backward_hbm_gbs": fb_kernel_bytes(G, B, True) / (ph["backward"] / args.steps / 1e3) / 1e9,
+            "gathered_bytes_per_launch": float(G.nnz) * B * 4,
+            "backward_hbm_gbs": fb_kernel_bytes(G, B, True) / (ph["backward"] / steps / 1e3) / 1e9,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     # end to end through the public API: X copied from pinned host memory
     # every step, forward + backward + optimiser step, the objective read back
@@ -784,7 +1136,7 @@ def autograd_arm(args):
     opt_e = mq.PGAMomentum([Xe], lr=wl["lr"], momentum=wl["momentum"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         with torch.no_grad():
             Xe.copy_(Xh, non_blocking=True)
         opt_e.zero_grad(set_to_none=False)
@@ -794,27 +1146,52 @@ def autograd_arm(args):
         obj.detach().cpu()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    ms_e2e, e2e_value = aggregate_ranks(t_e2e * 1e3, eu_step * args.steps, dist, "cuda")
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_autograd_sample(G, B, lam)
+    ms_e2e, e2e_value = aggregate_ranks(t_e2e * 1e3, eu_step * steps, dist, "cuda")
+    g.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1 if dist is None else dist.get_world_size(),
+        "steps": steps, "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f_B objective reduced in f64)", "data": "synthetic",
+        "config": {"workload": wl["desc"], "nnz": G.nnz, "nodes": G.n, "batch": B,
+                   "edge_updates_per_step": eu_step, "l2": "inputs larger than L2 (X 256 MB)",
+                   "parallelism": "replicas x1" if dist is None else f"replicas x{dist.get_world_size()}"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": G.n * B * 4, "d2h_bytes_per_step": B * 8,
+                "note": "the 256 MB host-to-device copy of X every step dominates this figure"},
+        "gpu_launches": launches_per_step * steps,
+        "kernel_ms_per_step": {k: v / steps for k, v in ph.items()},
+        "clocks": clocks,
+    }
+    if cpu:
+        line["cpu_baseline"] = oracle_autograd_sample(G, B, lam, target_s=cpu_target_s)
+    return line
+
+
+def app_b_arm(args):
+    """--workload app_b: the App. B relaxation comparison as one JSON line."""
+    import torch
+    import paper_2605_06921_gb300 as mq
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps({"app_b": app_b_record(mq, 0, not args.no_cpu)}))
+    return 0
+
+
+def autograd_arm(args):
+    import torch
+    import paper_2605_06921_gb300 as mq
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = autograd_measure(mq, args.steps, args.warmup, local=local, rank=rank, dist=dist,
+                            cpu=rank == 0 and world == 1 and not args.no_cpu)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["desc"], "nnz": G.nnz, "nodes": G.n, "batch": B,
-                       "edge_updates_per_step": eu_step, "l2": "inputs larger than L2 (X 256 MB)",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": roof,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": G.n * B * 4,
-                    "d2h_bytes_per_step": B * 8},
-            "gpu_launches": launches_per_step * args.steps,
-            "kernel_ms_per_step": {k: v / args.steps for k, v in ph.items()},
-            "clocks": clocks,
-        }
-        if cpu:
-            line["cpu_baseline"] = cpu
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -855,12 +1232,14 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="mis_batched", choices=sorted(WORKLOADS) + ["autograd_powerlaw"])
+    ap.add_argument("--workload", default="mis_batched", choices=sorted(WORKLOADS) + ["autograd_powerlaw", "app_b"])
     ap.add_argument("--x-dtype", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--v-dtype", default=None, choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="same as --no-sub")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: leave out the sub-records (steady state, other configurations)")
     ap.add_argument("--pool-k", type=int, default=0, help="pmQO pool of K sets per graph (0: Alg. 1/2)")
     ap.add_argument("--objective", default="fb", choices=sorted(OBJECTIVES), help="MaxCut relaxation")
     ap.add_argument("--rho", type=float, default=None, help="override the workload's reset fraction rho")
@@ -871,6 +1250,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.no_compare:
+        args.no_sub = True
     if args.rho is not None:
         WORKLOADS[args.workload]["rho"] = args.rho
     if args.rho_sweep:
@@ -881,6 +1262,8 @@ def main():
         return reference_arm(args)
     if args.workload == "autograd_powerlaw":
         return autograd_arm(args)
+    if args.workload == "app_b":
+        return app_b_arm(args)
     return gpu_arm(args)
 
 

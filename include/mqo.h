@@ -129,6 +129,7 @@ typedef struct {
   int64_t gain_descent; /* sum of the strict improvements accepted from later descents
                            (global-reset rounds and restarts; pool merges in pool mode) */
   int64_t gain_ls;      /* sum of the strict improvements accepted from local search */
+  int64_t steps;        /* descent steps taken in all (ticks that ran a gradient step) */
 } mqo_traj_info;
 
 /* ---------------------------------------------------------------- graphs */
@@ -294,11 +295,14 @@ MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
  * global-memory kernel), bit 1 = the discrete passes run fused, one CTA per
  * member graph (else three node-parallel launches), bit 2 = the
  * shared-memory step kernel uses 16-byte lanes (twice the trajectories per
- * lane, twice the rows per warp), bits 4.. = trajectories per lane of the
- * global-memory step kernel (0 with bit 0); *smem_bytes = the step kernel's
- * dynamic shared memory per CTA; *items = CTAs
- * per step (node ranges of at most 256 nodes); *replicas = counter
- * replicas per trajectory.
+ * lane, twice the rows per warp), bit 3 = the global-memory step runs as the
+ * staged-gather kernel (each CTA copies every neighbour row of x of a slice
+ * of rows into shared memory before summing), bits 4..7 = trajectories per
+ * lane of a global-memory step kernel (0 with bit 0), bits 8.. = KB of
+ * gathered rows of x per staged slice (0 without bit 3); *smem_bytes = the
+ * shared-memory step kernel's dynamic shared memory per CTA; *items = work
+ * items (node ranges of at most 256 nodes); *replicas = counter replicas per
+ * trajectory.
  */
 MQO_API mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_bytes, int32_t* items,
                                    int32_t* replicas);

@@ -73,6 +73,7 @@ class OrcState(C.Structure):
         ("ev_value", C.c_int64), ("ev_a", C.c_int64), ("ev_b", C.c_int64),
         ("accepts", C.c_int64), ("descents", C.c_int64), ("held", C.c_int64),
         ("first_value", C.c_int64), ("gain_descent", C.c_int64), ("gain_ls", C.c_int64),
+        ("steps", C.c_int64),
     ]
 
     def as_dict(self):

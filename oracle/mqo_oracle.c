@@ -107,6 +107,7 @@ typedef struct {
   int64_t first_value; /* INT64_MIN until the first acceptance */
   int64_t gain_descent;
   int64_t gain_ls;
+  int64_t steps;       /* descent steps taken in all */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -929,6 +930,7 @@ static void tick(orc_traj* T) {
     memcpy(T->V, T->Vn, (size_t)T->g->n * sizeof(float));
     st->ev_value = ev[0]; st->ev_a = ev[1]; st->ev_b = ev[2];
     st->s += 1;
+    st->steps += 1;
     st->last_round = ORC_R_NONE;
     st->last_commits = 0;
   } else {
@@ -1091,6 +1093,7 @@ static void tick_pool(orc_traj* T, int dec, const uint8_t* base, int ls_me) {
     memcpy(T->V, T->Vn, (size_t)n * sizeof(float));
     st->ev_value = ev[0]; st->ev_a = ev[1]; st->ev_b = ev[2];
     st->s += 1;
+    st->steps += 1;
     st->last_round = ORC_R_NONE;
     st->last_commits = 0;
   } else if (round != ORC_R_NONE) {

@@ -44,6 +44,16 @@ class Params(C.Structure):
     ]
 
 
+def _plan(p):
+    """Decode the plan word of mqo_solver_info / mqo_autotune."""
+    if p & 1:
+        kern = "smem_wide" if p & 4 else "smem"
+    else:
+        kern = "staged" if p & 8 else "global"
+    return {"step_kernel": kern, "discrete_kernel": "graph" if p & 2 else "pairs", "lanes_vec": (p >> 4) & 15,
+            "slice_kb": p >> 8}
+
+
 class TrajInfo(C.Structure):
     _fields_ = [
         ("phase", C.c_int32), ("s", C.c_int32), ("r", C.c_int32), ("o", C.c_int32),
@@ -51,6 +61,7 @@ class TrajInfo(C.Structure):
         ("last_commits", C.c_int64), ("ev_value", C.c_int64), ("ev_a", C.c_int64), ("ev_b", C.c_int64),
         ("accepts", C.c_int64), ("descents", C.c_int64), ("held", C.c_int64),
         ("first_value", C.c_int64), ("gain_descent", C.c_int64), ("gain_ls", C.c_int64),
+        ("steps", C.c_int64),
     ]
 
     def as_dict(self):
@@ -274,21 +285,17 @@ class Solver:
         return vals, bits
 
     def info(self):
-        """Execution plan: step kernel (1 shared-memory staged, 0 global), smem bytes, items, counter replicas."""
+        """Execution plan: step kernel (smem, smem_wide, staged or global), discrete kernel, trajectories per
+        lane, KB of gathered rows per staged slice, smem bytes, items, counter replicas."""
         k, sm, it, r = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
         _check(lib().mqo_solver_info(self.handle, C.byref(k), C.byref(sm), C.byref(it), C.byref(r)))
-        return {"step_kernel": ("smem_wide" if k.value & 4 else "smem") if k.value & 1 else "global",
-                "discrete_kernel": "graph" if k.value & 2 else "pairs", "lanes_vec": k.value >> 4,
-                "smem_bytes": sm.value, "items": it.value, "replicas": r.value}
+        return dict(_plan(k.value), smem_bytes=sm.value, items=it.value, replicas=r.value)
 
     def autotune(self, ticks=10):
         """Time every launch plan over `ticks` ticks (state restored after each) and keep the fastest."""
         plan, ms = C.c_int32(), C.c_double()
         _check(lib().mqo_autotune(self.handle, int(ticks), C.byref(plan), C.byref(ms)))
-        p = plan.value
-        return {"step_kernel": ("smem_wide" if p & 4 else "smem") if p & 1 else "global",
-                "discrete_kernel": "graph" if p & 2 else "pairs",
-                "lanes_vec": p >> 4, "ms_per_tick": ms.value}
+        return dict(_plan(plan.value), ms_per_tick=ms.value)
 
     def pool_state(self):
         """Pool mode: (counts [G], values [G, K], merges [G]) on the host and the
@@ -306,6 +313,12 @@ class Solver:
         arr = (TrajInfo * self.T)()
         _check(lib().mqo_traj_state(self.handle, arr))
         return [a.as_dict() for a in arr]
+
+    def steps_taken(self):
+        """Descent steps taken so far by every trajectory (int64 array [T])."""
+        arr = (TrajInfo * self.T)()
+        _check(lib().mqo_traj_state(self.handle, arr))
+        return np.array([a.steps for a in arr], dtype=np.int64)
 
     def get_x(self):
         t = self._torch.empty(self.graph.n * self.B, dtype=getattr(self._torch, _TORCH_DT[self.p.x_dtype]),

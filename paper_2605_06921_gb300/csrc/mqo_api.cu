@@ -17,6 +17,7 @@
 
 #include "../../include/mqo.h"
 #include "mqo_host.h"
+#include "mqo_step.cuh"
 
 using namespace mqo;
 
@@ -38,6 +39,7 @@ constexpr int kChunkNodes = kItemMaxNodes;  // nodes per item
 constexpr int kSplit = 512;       // row length above which the f_B kernels chunk a row
 constexpr size_t kStepSmemLimit = 110 * 1024;  // shared-memory step kernel if the graph block fits
 constexpr size_t kDiscSmemLimit = 160 * 1024;  // fused discrete kernel if the graph's bit words fit
+constexpr int kDefaultSliceKB = 32;  // staged step kernel: gathered x rows per slice (KB)
 
 }  // namespace
 
@@ -112,6 +114,15 @@ struct mqo_solver_s {
   void* d_save = nullptr;
   std::vector<void*> allocs;
   size_t x_bytes = 0, v_bytes = 0, words = 0, pairs = 0;
+  // staged-gather step kernel: device slice arrays per capacity (KB of
+  // gathered rows of x), built on first use
+  struct SliceSet {
+    int cap_kb = 0;
+    Slice* d = nullptr;
+    int32_t count = 0, rows = 0, cols = 0;
+  };
+  std::vector<SliceSet> slice_sets;
+  bool staged_ok = false;  // every row's neighbour rows fit the largest capacity
 };
 
 namespace {
@@ -127,6 +138,44 @@ mqo_status dalloc(T** p, size_t count, std::vector<void*>* track) {
 }
 
 size_t dtype_size(int d) { return d == DT_F32 ? 4 : 2; }
+
+// Slices of the staged-gather step kernel: walk every work item's rows in
+// order and cut a slice before the row that would take it past `rows` rows
+// or `cols` CSR entries.  False if one row alone has more than `cols` entries.
+bool build_slices(const mqo_graph_s* g, int32_t rows, int32_t cols, std::vector<Slice>& out) {
+  out.clear();
+  for (int32_t it = 0; it < g->num_items; ++it) {
+    const Item& item = g->h_items[(size_t)it];
+    int32_t v0 = item.v0;
+    while (v0 < item.v1) {
+      int32_t v1 = v0;
+      int64_t c = 0;
+      while (v1 < item.v1 && v1 - v0 < rows) {
+        const int64_t d = g->h_rp[(size_t)v1 + 1] - g->h_rp[(size_t)v1];
+        if (d > cols) return false;
+        if (c + d > cols) break;
+        c += d;
+        v1 += 1;
+      }
+      out.push_back(Slice{item.g, it, v0, v1});
+      v0 = v1;
+    }
+  }
+  return true;
+}
+
+// rows and CSR entries of one staged slice for `cap_kb` KB of gathered x rows
+void slice_shape(int B, int x_dtype, int cap_kb, int32_t* rows, int32_t* cols) {
+  const int rowx = B * (int)dtype_size(x_dtype);
+  *cols = std::max(1, cap_kb * 1024 / rowx);
+  *rows = std::min<int32_t>(128, std::max<int32_t>(8, *cols / 2));
+}
+
+// the staged kernel needs 16-byte multiples for a row of x and of V
+bool staged_possible(int B, int x_dtype, int v_dtype) {
+  return (B * (int)dtype_size(x_dtype)) % 16 == 0 && (B * (int)dtype_size(v_dtype)) % 16 == 0 && B <= 256 &&
+         staged_vec_ok(B, x_dtype, default_staged_vec(B, x_dtype));
+}
 
 // Host checks of the CSR structure (sizes, row pointers): O(n).
 mqo_status validate_structure(int64_t n, int64_t nnz, const int64_t* rp) {
@@ -431,6 +480,43 @@ mqo_status poison(mqo_solver s, cudaError_t e, const char* what) {
     if ((s)->poisoned) return fail(MQO_ESTATE, "solver poisoned by an earlier error"); \
   } while (0)
 
+// The staged kernel's slices for `cap_kb` KB of gathered x rows, built and
+// uploaded on first use; count < 0 if some row has too many entries for it.
+mqo_solver_s::SliceSet slice_set(mqo_solver s, int cap_kb) {
+  for (const auto& ss : s->slice_sets)
+    if (ss.cap_kb == cap_kb) return ss;
+  mqo_solver_s::SliceSet ss;
+  ss.cap_kb = cap_kb;
+  slice_shape(s->S.B, s->S.p.x_dtype, cap_kb, &ss.rows, &ss.cols);
+  std::vector<Slice> h;
+  const size_t smem = staged_layout(s->S.B, (int)dtype_size(s->S.p.x_dtype), (int)dtype_size(s->S.p.v_dtype), ss.cols,
+                                    ss.rows, true)
+                          .total;
+  if (smem > 200 * 1024 || !build_slices(s->g, ss.rows, ss.cols, h) || h.empty()) {
+    ss.count = -1;
+  } else if (dalloc(&ss.d, h.size(), &s->allocs) != MQO_OK ||
+             cudaMemcpy(ss.d, h.data(), h.size() * sizeof(Slice), cudaMemcpyHostToDevice) != cudaSuccess) {
+    ss.count = -1;
+  } else {
+    ss.count = (int32_t)h.size();
+  }
+  s->slice_sets.push_back(ss);
+  return ss;
+}
+
+void use_slices(mqo_solver s, const mqo_solver_s::SliceSet& ss) {
+  s->S.slices = ss.d;
+  s->S.num_slices = ss.count;
+  s->S.slice_rows = ss.rows;
+  s->S.slice_cols = ss.cols;
+}
+
+int slice_kb(mqo_solver s) {
+  for (const auto& ss : s->slice_sets)
+    if (ss.d == s->S.slices && ss.count > 0) return ss.cap_kb;
+  return 0;
+}
+
 cudaError_t enqueue_tick(mqo_solver s) {
   cudaError_t e;
   const SolverDev& S = s->S;
@@ -627,12 +713,24 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     while (R < 64 && R * 8 < max_items) R *= 2;
     S.R = R;
     const size_t need = step_smem_bytes(B, p->x_dtype, p->problem, max_ng);
-    // MQO_STEP_KERNEL=generic selects the global-memory step kernel even
-    // when the member graphs fit in shared memory
+    // Default step kernel: the shared-memory one when every member graph's
+    // block of x fits, else the staged-gather one when its slices fit, else
+    // the plain global-memory one.  MQO_STEP_KERNEL=generic | staged selects
+    // either global-memory kernel even when the member graphs fit in shared
+    // memory (staged: where possible).
     const char* force = getenv("MQO_STEP_KERNEL");
     const bool generic = force && strcmp(force, "generic") == 0;
+    const bool staged = force && strcmp(force, "staged") == 0;
     s->step_smem_max = (B >= 32 && need <= kStepSmemLimit) ? need : 0;
-    s->step_smem = generic ? 0 : s->step_smem_max;
+    s->step_smem = (generic || staged) ? 0 : s->step_smem_max;
+    if (staged_possible(B, p->x_dtype, p->v_dtype)) {
+      const mqo_solver_s::SliceSet ss = slice_set(s, kDefaultSliceKB);
+      if (ss.count > 0) {
+        s->staged_ok = true;
+        use_slices(s, ss);
+      }
+    }
+    s->S.step_staged = (s->staged_ok && !generic) ? 1 : 0;
     // MQO_STEP_KERNEL=wide: the shared-memory kernel with 16-byte lanes
     s->S.step_wide = force && strcmp(force, "wide") == 0 && step_wide_possible(B, p->x_dtype) ? 1 : 0;
     // The fused per-graph discrete kernel runs one CTA per member graph, so
@@ -940,10 +1038,15 @@ mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_byt
                            int32_t* replicas) {
   if (!s) return fail(MQO_EINVAL, "null solver");
   const int B = s->S.B;
-  const int vec = s->step_smem > 0 ? 0 : (s->S.step_vec > 0 ? s->S.step_vec : default_step_vec(B, s->S.p.x_dtype));
+  const bool staged = s->step_smem == 0 && s->S.step_staged;
+  const int vec = s->step_smem > 0 ? 0
+                  : (s->S.step_vec > 0 ? s->S.step_vec
+                                       : (staged ? default_staged_vec(B, s->S.p.x_dtype)
+                                                 : default_step_vec(B, s->S.p.x_dtype)));
   if (step_kernel)
     *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0) |
-                   (s->step_smem > 0 && s->S.step_wide ? 4 : 0) | (vec << 4);
+                   (s->step_smem > 0 && s->S.step_wide ? 4 : 0) | (staged ? 8 : 0) | (vec << 4) |
+                   ((staged ? slice_kb(s) : 0) << 8);
   if (smem_bytes) *smem_bytes = (int64_t)s->step_smem;
   if (items) *items = s->S.g.num_items;
   if (replicas) *replicas = s->S.R;
@@ -1024,6 +1127,7 @@ mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out) {
     o.first_value = t.first_value;
     o.gain_descent = t.gain_descent;
     o.gain_ls = t.gain_ls;
+    o.steps = t.steps;
   }
   return MQO_OK;
 }
@@ -1150,6 +1254,8 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     int vec;
     int wide;
     size_t disc_smem;
+    int staged;   // staged-gather step kernel
+    int slice_kb; // its slice capacity
   };
   std::vector<Plan> plans;
   std::vector<size_t> steps = {0};
@@ -1160,17 +1266,23 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
   for (size_t st : steps)
     for (size_t dc : discs) {
       if (st > 0) {
-        plans.push_back({st, 0, 0, dc});
-        if (wide_ok) plans.push_back({st, 0, 1, dc});
+        plans.push_back({st, 0, 0, dc, 0, 0});
+        if (wide_ok) plans.push_back({st, 0, 1, dc, 0, 0});
       } else {
         for (int v : {1, 2, 4, 8}) {
           // 16-byte lanes (8 trajectories) only for 16-bit x and momentum
           if (v == 8 && (S.p.x_dtype == DT_F32 || S.p.v_dtype == DT_F32)) continue;
-          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc});
+          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc, 0, 0});
         }
+        if (s->staged_ok)
+          for (int kb : {16, 32, 64}) {
+            if (slice_set(s, kb).count <= 0) continue;
+            for (int v : {2, 4, 8})
+              if (staged_vec_ok(B, S.p.x_dtype, v)) plans.push_back({0, v, 0, dc, 1, kb});
+          }
       }
     }
-  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem};
+  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem, S.step_staged, slice_kb(s)};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
@@ -1194,6 +1306,8 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
       S.step_vec = pl.vec;
       S.step_wide = pl.wide;
       s->disc_smem = pl.disc_smem;
+      S.step_staged = pl.staged;
+      if (pl.staged) use_slices(s, slice_set(s, pl.slice_kb));
       if (err == cudaSuccess) err = enqueue_tick(s);  // untimed first tick
       if (err == cudaSuccess) err = cudaEventRecord(e0, s->work);
       for (int32_t k = 0; k < ticks && err == cudaSuccess; ++k) err = enqueue_tick(s);
@@ -1216,24 +1330,28 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(snap);
+  auto apply = [&](const Plan& pl) {
+    s->step_smem = pl.step_smem;
+    S.step_vec = pl.vec;
+    S.step_wide = pl.wide;
+    s->disc_smem = pl.disc_smem;
+    S.step_staged = pl.staged;
+    if (pl.slice_kb > 0) use_slices(s, slice_set(s, pl.slice_kb));
+  };
   if (err != cudaSuccess) {
-    s->step_smem = keep.step_smem;
-    S.step_vec = keep.vec;
-    S.step_wide = keep.wide;
-    s->disc_smem = keep.disc_smem;
+    apply(keep);
     return poison(s, err, "mqo_autotune");
   }
-  s->step_smem = chosen.step_smem;
-  S.step_vec = chosen.vec;
-  S.step_wide = chosen.wide;
-  s->disc_smem = chosen.disc_smem;
+  apply(chosen);
   // the captured tick graphs hold the old launch configuration
   if (s->gx1) cudaGraphExecDestroy(s->gx1);
   if (s->gx16) cudaGraphExecDestroy(s->gx16);
   s->gx1 = s->gx16 = nullptr;
-  if (plan_out)
+  if (plan_out) {
+    const bool stg = chosen.step_smem == 0 && chosen.staged;
     *plan_out = (chosen.step_smem > 0 ? 1 : 0) | (chosen.disc_smem > 0 ? 2 : 0) | (chosen.wide ? 4 : 0) |
-                (chosen.vec << 4);
+                (stg ? 8 : 0) | (chosen.vec << 4) | ((stg ? chosen.slice_kb : 0) << 8);
+  }
   if (best_ms_per_tick) *best_ms_per_tick = best / ticks;
   return MQO_OK;
 }

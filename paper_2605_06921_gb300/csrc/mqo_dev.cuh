@@ -73,6 +73,7 @@ struct __align__(16) TrajState {
   // gradient updates), then the strict improvements accepted from later
   // descents (global resets, restarts) and from local search
   int64_t first_value, gain_descent, gain_ls;
+  int64_t steps;  // descent steps taken in all
 };
 
 // book a strict improvement of st.best to `value` by its source
@@ -106,6 +107,13 @@ struct Item {
   int32_t g, v0, v1, pad;
 };
 
+// A node range [v0, v1) inside work item `it` of member graph g: the unit of
+// the staged-gather step kernel (at most slice_rows rows whose CSR rows hold
+// at most slice_cols entries together).
+struct Slice {
+  int32_t g, it, v0, v1;
+};
+
 struct GraphDev {
   int32_t n, num_graphs;
   int64_t nnz;
@@ -127,6 +135,9 @@ struct SolverDev {
   int32_t step_vec; // trajectories per lane of the global-memory step kernel (0: B/32 or 1)
   int32_t step_wide; // shared-memory step kernel with 16-byte lanes
   int32_t split;    // CTAs per item of the node-parallel kernels (several when there are few items)
+  int32_t step_staged;  // 1: staged-gather step kernel (when the shared-memory one is not used)
+  const Slice* slices;  // its slices, their count, and the most rows / CSR entries of one slice
+  int32_t num_slices, slice_rows, slice_cols;
   void* X0;         // relaxed x: tick t reads X[t&1] and writes X[(t+1)&1]
   void* X1;
   void* V;          // momentum

@@ -10,6 +10,10 @@
 // and a second kernel adds a row's chunk partials in chunk order.  The
 // objective is accumulated per lane in float32 over a few rows, then in
 // double, then reduced per block and across blocks with double atomics.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
 #include "mqo_dev.cuh"
 #include "mqo_host.h"
 
@@ -194,9 +198,197 @@ __global__ void __launch_bounds__(256) k_fb_heavy(FbArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- pipelined units
+// B >= 32: one warp is one row group (lane l owns columns l*VEC ..).  Each
+// warp walks its units (light rows and 512-entry chunks, as k_fb_units) as
+// one stream of batches of at most `pipe` CSR entries (pipe * B * 4 bytes =
+// 4 KB): the neighbour rows of x of the next batch are copied into the
+// warp's other shared-memory buffer with cp.async while the current batch
+// is summed, so every warp keeps a batch of gathers in flight across unit
+// boundaries.  The sums run over each unit's entries in CSR order, exactly
+// as in k_fb_units.
+constexpr int kFbPipeBytes = 4096;  // gathered bytes per batch and warp
+constexpr int kFbPipeThreads = 256;
+
+// MQO_FB_KERNEL=units selects the plain unit kernel for every batch size
+// (read at every launch, so that a test can compare the two)
+bool fb_pipe_enabled() {
+  const char* e = getenv("MQO_FB_KERNEL");
+  return !(e && strcmp(e, "units") == 0);
+}
+
+__device__ __forceinline__ void fb_cp_async16(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+struct FbUnit {
+  int64_t row;
+  int32_t j0, j1;
+  bool whole, valid;
+};
+
+__device__ __forceinline__ FbUnit fb_unit(const FbArgs& a, int64_t u, int64_t nunits) {
+  FbUnit r;
+  r.valid = u < nunits;
+  r.whole = true;
+  r.row = 0;
+  r.j0 = r.j1 = 0;
+  if (!r.valid) return r;
+  if (u < a.hp.num_light) {
+    r.row = a.hp.light_rows[u];
+    r.j0 = a.g.row_ptr[r.row];
+    r.j1 = a.g.row_ptr[r.row + 1];
+  } else {
+    const int64_t c = u - a.hp.num_light;
+    r.whole = false;
+    r.row = a.hp.heavy_row[c];
+    r.j0 = a.hp.heavy_j0[c];
+    r.j1 = a.hp.heavy_j1[c];
+  }
+  return r;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_fb[];
+  __shared__ double s_obj[256];
+  constexpr int B = 32 * VEC;
+  constexpr int ROWB = B * 4;
+  constexpr int PIPE = kFbPipeBytes / ROWB < 32 ? kFbPipeBytes / ROWB : 32;
+  constexpr int PER = ROWB / 16;  // 16-byte pieces of one row
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int b0 = lane * VEC;
+  unsigned char* buf = smem_fb + (size_t)warp * 2 * PIPE * ROWB;
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nunits = (int64_t)a.hp.num_light + a.hp.num_chunks;
+  const bool want_obj = a.obj != nullptr;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_obj[i] = 0.0;
+  __syncthreads();
+  float objf[VEC];
+  double objd[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) { objf[e] = 0.0f; objd[e] = 0.0; }
+  int pending = 0;
+
+  // copy the rows of entries [j, j + cnt) into buffer `slot`; lane e < cnt
+  // returns entry j+e's column index and weight in c / w
+  auto issue = [&](int32_t j, int cnt, int slot, int32_t& c, int& w) {
+    c = 0;
+    w = 1;
+    if (lane < cnt) {
+      c = __ldcs(a.g.col + j + lane);
+      if (a.g.w) w = a.g.w[j + lane];
+    }
+    unsigned char* dst = buf + (size_t)slot * PIPE * ROWB;
+    for (int k = lane; k < cnt * PER; k += 32) {
+      const int e = k / PER;
+      const int piece = k - e * PER;
+      const int32_t ue = __shfl_sync(0xffffffffu, c, e);
+      fb_cp_async16(dst + e * ROWB + piece * 16,
+                    reinterpret_cast<const unsigned char*>(a.X + (int64_t)ue * B) + piece * 16);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  FbUnit cur = fb_unit(a, u, nunits);
+  int32_t jb = cur.j0;  // first entry of the current batch
+  int slot = 0;
+  int32_t cidx;
+  int wcur, wnext;
+  issue(jb, cur.valid ? min(PIPE, cur.j1 - jb) : 0, slot, cidx, wcur);
+  float acc[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+  while (cur.valid) {
+    // the batch after this one: the rest of this unit, or the next unit
+    FbUnit nxt = cur;
+    int64_t un = u;
+    int32_t jn = jb + PIPE;
+    if (jn >= cur.j1) {
+      un = u + W;
+      nxt = fb_unit(a, un, nunits);
+      jn = nxt.j0;
+    }
+    issue(jn, nxt.valid ? min(PIPE, nxt.j1 - jn) : 0, slot ^ 1, cidx, wnext);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncwarp();
+    const int cnt = min(PIPE, cur.j1 - jb);
+    const unsigned char* src = buf + (size_t)slot * PIPE * ROWB + b0 * 4;
+    for (int e = 0; e < cnt; ++e) {
+      const int w = __shfl_sync(0xffffffffu, wcur, e);
+      float f[VEC];
+      if constexpr (VEC == 1) {
+        f[0] = *reinterpret_cast<const float*>(src + e * ROWB);
+      } else if constexpr (VEC == 2) {
+        const float2 p = *reinterpret_cast<const float2*>(src + e * ROWB);
+        f[0] = p.x;
+        f[1] = p.y;
+      } else {
+#pragma unroll
+        for (int q = 0; q < VEC; q += 4) {
+          const float4 p = *reinterpret_cast<const float4*>(src + e * ROWB + q * 4);
+          f[q] = p.x;
+          f[q + 1] = p.y;
+          f[q + 2] = p.z;
+          f[q + 3] = p.w;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[q] = w >= 0 ? acc[q] + f[q] : acc[q] - f[q];
+    }
+    __syncwarp();
+    if (jb + PIPE >= cur.j1) {  // the unit is complete
+      if (cur.whole) {
+        FbOut<VEC>::emit(cur.row, acc, a.X, B, b0, a.lambda_, a.gout, a.G, want_obj, objf);
+        if (++pending == 16) flush_obj<VEC>(objf, objd, pending);
+      } else {
+        const int64_t c = u - a.hp.num_light;
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) a.scratch[c * B + b0 + q] = acc[q];
+      }
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[q] = 0.0f;
+    }
+    cur = nxt;
+    u = un;
+    jb = jn;
+    slot ^= 1;
+    wcur = wnext;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (want_obj) {
+    flush_obj<VEC>(objf, objd, pending);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+      if (objd[e] != 0.0) atomicAdd(&s_obj[b0 + e], objd[e]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+      if (s_obj[i] != 0.0) atomicAdd(&a.obj[i], s_obj[i]);
+  }
+}
+
 template <int VEC>
 static cudaError_t launch_fb_vec(const FbArgs& a, int grid, cudaStream_t s) {
-  if ((int64_t)a.hp.num_light + a.hp.num_chunks > 0) k_fb_units<VEC><<<grid, 256, 0, s>>>(a);
+  if ((int64_t)a.hp.num_light + a.hp.num_chunks > 0) {
+    if (a.B == 32 * VEC && fb_pipe_enabled()) {
+      constexpr int ROWB = 32 * VEC * 4;
+      constexpr int PIPE = kFbPipeBytes / ROWB < 32 ? kFbPipeBytes / ROWB : 32;
+      const size_t smem = (size_t)(kFbPipeThreads / 32) * 2 * PIPE * ROWB;
+      cudaError_t e = cudaFuncSetAttribute(k_fb_pipe<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      // one wave: the resident CTAs of every SM (each warp strides over the units)
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fb_pipe<VEC>, kFbPipeThreads, smem);
+      if (e != cudaSuccess) return e;
+      const int pgrid = std::max(1, std::min(grid, per_sm * (grid / 8)));
+      k_fb_pipe<VEC><<<pgrid, kFbPipeThreads, smem, s>>>(a);
+    } else {
+      k_fb_units<VEC><<<grid, 256, 0, s>>>(a);
+    }
+  }
   if (a.hp.num_heavy > 0) k_fb_heavy<VEC><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

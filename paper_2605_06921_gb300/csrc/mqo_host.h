@@ -16,6 +16,8 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
                         size_t smem, cudaStream_t stream);
 bool step_wide_possible(int B, int x_dtype);
 int default_step_vec(int B, int x_dtype);
+bool staged_vec_ok(int B, int x_dtype, int vec);
+int default_staged_vec(int B, int x_dtype);
 size_t step_smem_bytes(int B, int x_dtype, int problem, int max_ng);
 
 cudaError_t launch_ctrl(const SolverDev& S, int mode, const uint8_t* mask, cudaStream_t stream);

@@ -343,7 +343,19 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   a.act = act;
   a.gflag_step = gflag_step;
   a.tick = S.tick;
+  a.slices = S.slices;
+  a.num_slices = S.num_slices;
+  a.slice_rows = S.slice_rows;
+  a.slice_cols = S.slice_cols;
   const int xd = S.p.x_dtype, vd = S.p.v_dtype;
+  if (smem == 0 && S.step_staged) {
+    // staged-gather kernel: one CTA per slice
+    const int vec = S.step_vec > 0 ? S.step_vec : default_staged_vec(S.B, xd);
+    const size_t qs = staged_layout(S.B, xd == DT_F32 ? 4 : 2, vd == DT_F32 ? 4 : 2, S.slice_cols, S.slice_rows,
+                                    S.g.w != nullptr && S.p.problem != PROB_MIS)
+                          .total;
+    return launch_step_staged(a, vec, xd, vd, qs, stream);
+  }
   if (smem == 0) {
     // global-memory kernel; few items (a handful of member graphs): several CTAs per item
     const int vec = S.step_vec > 0 ? S.step_vec : default_step_vec(S.B, xd);

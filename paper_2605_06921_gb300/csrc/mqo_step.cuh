@@ -41,10 +41,36 @@
 
 namespace mqo {
 
+// Staged-gather step kernel (mqo_step_staged.cu): CTAs of kStagedThreads
+// threads, one Slice each (mqo_dev.cuh).
+constexpr int kStagedThreads = 256;
+
+// Byte offsets of the staged kernel's shared memory: counters, slice row
+// pointers, column indices, weights, own rows of x and V, gathered rows.
+struct StagedLayout {
+  size_t cnt, rp, col, w, xo, vo, nb, total;
+};
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ __forceinline__ StagedLayout staged_layout(int B, int sx, int sv, int cols, int rows,
+                                                                bool weighted) {
+  StagedLayout L;
+  L.cnt = 0;
+  L.rp = L.cnt + align16((size_t)3 * B * 8);
+  L.col = L.rp + align16((size_t)(rows + 1) * 4);
+  L.w = L.col + align16((size_t)cols * 4);
+  L.xo = L.w + (weighted ? align16((size_t)cols) : 0);
+  L.vo = L.xo + align16((size_t)rows * B * sx);
+  L.nb = L.vo + align16((size_t)rows * B * sv);
+  L.total = L.nb + align16((size_t)cols * B * sx);
+  return L;
+}
+
 struct StepArgs {
   GraphDev g;
   int32_t B, Bw, R, problem, objective;
   int32_t split;  // generic kernel: CTAs per item, each taking a contiguous slice of its rows
+  const Slice* slices;  // staged kernel: its slices, their count, and the most rows and CSR entries of one
+  int32_t num_slices, slice_rows, slice_cols;
   float alpha, momentum, gamma, lambda_;
   void* X0;
   void* X1;
@@ -143,5 +169,10 @@ __device__ __forceinline__ void flush_step_counters(const StepArgs& a, unsigned 
 // the global-memory step kernel (mqo_step_generic.cu) for the given storage
 // types and trajectories per lane
 cudaError_t launch_step_generic(const StepArgs& a, int vec, int x_dtype, int v_dtype, int grid, cudaStream_t s);
+// the staged-gather step kernel (mqo_step_staged.cu), `smem` bytes of
+// dynamic shared memory (staged_layout(...).total)
+cudaError_t launch_step_staged(const StepArgs& a, int vec, int x_dtype, int v_dtype, size_t smem, cudaStream_t s);
+bool staged_vec_ok(int B, int x_dtype, int vec);
+int default_staged_vec(int B, int x_dtype);
 
 }  // namespace mqo

@@ -197,6 +197,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
     if (st.phase == PH_DESCENT) {
       act |= ACT_STEP;
       st.s += 1;
+      st.steps += 1;
       st.last_round = RD_NONE;
       round = RD_NONE;
     } else if (round != RD_NONE) {
@@ -279,6 +280,7 @@ __device__ __forceinline__ void ctrl_one(const CtrlArgs& A, int64_t tau, const C
     if (st.phase == PH_DESCENT) {
       act |= ACT_STEP;
       st.s += 1;
+      st.steps += 1;
       st.last_round = RD_NONE;
       round = RD_NONE;
     } else {
@@ -973,6 +975,7 @@ __global__ void k_state_init(SolverDev S) {
     st.held = (int64_t)(-9223372036854775807LL - 1);
     st.first_value = st.held;
     st.gain_descent = st.gain_ls = 0;
+    st.steps = 0;
     S.st[tau] = st;
     if (S.K > 0 && tau < S.g.num_graphs) {
       PoolState ps;

@@ -124,3 +124,43 @@ def test_momentum_and_adam_match_torch(mq, graph_and_x):
             with torch.no_grad():
                 xb.clamp_(-1.0, 1.0)
         assert torch.allclose(xa, xb, rtol=1e-5, atol=1e-5), kind
+
+
+@pytest.mark.parametrize("B,signed", [(32, False), (64, False), (64, True), (128, False), (256, True)])
+def test_pipelined_kernel_equals_unit_kernel_and_oracle(mq, monkeypatch, B, signed):
+    """B >= 32 takes the warp-pipelined kernel (neighbour rows staged through
+    shared memory a batch ahead): its gradient equals the unit kernel's bit
+    for bit (same CSR-order sums per row and per 512-entry chunk) and the
+    oracle's float64 gradient within the float32 rounding of the sums; its
+    objective matches the oracle's."""
+    G = power_law_with_hub(6000, 1500, seed=B)
+    if signed:
+        rows, cols = G.edges_directed()
+        up = rows < cols
+        w = np.random.default_rng(B).choice(np.array([-1, 1], dtype=np.int8), size=int(up.sum()))
+        G = mi.from_edges(G.n, rows[up], cols[up], w)
+    assert G.degrees().max() > 512
+    g = mq.Graph(G)
+    lam = 0.001
+    Xh = (np.random.default_rng(B + 1).random((G.n, B)) * 2 - 1).astype(np.float32)
+    X = torch.from_numpy(Xh).cuda()
+    gout = torch.linspace(0.5, 2.0, B, device="cuda")
+    got = mq.spmm_grad(g, X, lam, gout)
+    obj = mq.fb_forward(g, X, lam).cpu().numpy()
+    monkeypatch.setenv("MQO_FB_KERNEL", "units")
+    want_units = mq.spmm_grad(g, X, lam, gout)
+    monkeypatch.delenv("MQO_FB_KERNEL")
+    torch.cuda.synchronize()
+    assert torch.equal(got, want_units)
+    og = oracle.Graph(G)
+    gh = got.cpu().numpy().astype(np.float64)
+    deg = np.diff(G.row_ptr)
+    rows = np.repeat(np.arange(G.n), deg)
+    go = gout.cpu().numpy().astype(np.float64)
+    for b in range(0, B, max(1, B // 8)):
+        xb = Xh[:, b].astype(np.float64)
+        want = oracle.gradient_f64(og, oracle.MAXCUT, 0.0, lam, xb) * go[b]
+        absum = np.bincount(rows, weights=np.abs(Xh[G.col_idx, b].astype(np.float64)), minlength=G.n)
+        assert np.all(np.abs(gh[:, b] - want) <= 1e-5 * go[b] * (lam + 2 * absum) + 1e-7), b
+        wobj = oracle.objective_f64(og, oracle.MAXCUT, 0.0, lam, xb)
+        assert obj[b] == pytest.approx(wobj, rel=2e-6, abs=1e-3), b

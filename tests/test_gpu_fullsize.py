@@ -51,7 +51,7 @@ def sampled_machine_check(mq, G, p, warm, ticks, samples, timed=True):
         tr.run(total)
         lo, hi = int(G.node_offsets[g]), int(G.node_offsets[g + 1])
         for key in ("phase", "s", "r", "o", "best", "ticks", "ev_value", "ev_a", "ev_b", "accepts", "descents",
-                    "first_value", "gain_descent", "gain_ls"):
+                    "first_value", "gain_descent", "gain_ls", "steps"):
             assert states[t][key] == tr.state[key], (g, b, key, states[t][key], tr.state[key])
         assert vals[t] == tr.state["best"]
         assert np.array_equal(z[lo:hi, b], tr.zbest)

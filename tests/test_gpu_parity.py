@@ -158,6 +158,41 @@ def test_wide_lane_step_kernel(mq, monkeypatch, problem, B, xd, vd):
     assert s.info()["step_kernel"] == "smem_wide"
 
 
+@pytest.mark.parametrize("problem,weighted", [(0, False), (1, False), (1, True)])
+@pytest.mark.parametrize("B,xd,vd", [(8, 2, 2), (16, 2, 2), (16, 2, 0), (32, 1, 1), (8, 0, 0), (64, 0, 0),
+                                     (128, 1, 1), (128, 1, 0)])
+def test_staged_step_kernel(mq, monkeypatch, problem, weighted, B, xd, vd):
+    """the staged-gather step kernel (the default for graphs too large for
+    shared memory) on small graphs; with 256-byte rows of x (B = 128 in
+    16-bit, B = 64 in float32) every work item spans many slices"""
+    monkeypatch.setenv("MQO_STEP_KERNEL", "staged")
+    monkeypatch.setenv("MQO_DISC_KERNEL", "pairs")
+    G = small_batch(3, 60, 300, 0.05, seed=B + xd)
+    if weighted:
+        G = signed(G, B)
+    p = mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, alpha=0.8 if problem == 0 else 0.05,
+                  momentum=0.5, seed=B + 11)
+    s = _plain_steps(mq, G, p, 8)
+    assert s.info()["step_kernel"] == "staged" and s.info()["slice_kb"] == 32
+    G = small_batch(2, 30, 60, 0.15, seed=B + 9)
+    if weighted:
+        G = signed(G, B + 1)
+    s, _ = _machine(mq, G, mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, t_gs=3, descent_cap=20,
+                                     seed=9), 150)
+    assert s.info()["step_kernel"] == "staged"
+
+
+def test_staged_step_kernel_falls_back_on_long_rows(mq, monkeypatch):
+    """a row whose neighbour rows of x exceed one slice (a star of 300 leaves,
+    256-byte rows: 75 KB): the plain global-memory kernel takes the step"""
+    monkeypatch.setenv("MQO_STEP_KERNEL", "staged")
+    star = mi.from_edges(301, np.zeros(300, int), np.arange(1, 301))
+    G = mi.pack([star, mi.erdos_renyi(80, 0.1, 4)])
+    p = mq.params(problem=1, batch=128, x_dtype=1, alpha=0.05, momentum=0.5, seed=4)
+    s = _plain_steps(mq, G, p, 6)
+    assert s.info()["step_kernel"] == "global"
+
+
 @pytest.mark.parametrize("xd,vd", [(1, 1), (1, 0), (2, 2), (2, 0)])
 @pytest.mark.parametrize("B", [16, 32, 128])
 def test_plain_steps_low_precision_mis(mq, xd, vd, B):
@@ -242,7 +277,7 @@ def _machine(mq, G, p, nticks, trace=0, tune_at=None):
             want = tr.state
             got = states[t]
             for key in ("phase", "s", "r", "o", "best", "ticks", "last_round", "last_commits", "ev_value", "ev_a",
-                        "ev_b", "accepts", "descents", "first_value", "gain_descent", "gain_ls"):
+                        "ev_b", "accepts", "descents", "first_value", "gain_descent", "gain_ls", "steps"):
                 assert got[key] == want[key], (g, b, key, got[key], want[key])
             assert vals[t] == want["best"]
             assert np.array_equal(z[lo:hi, b], tr.zbest), (g, b)

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 KEYS = ("phase", "s", "r", "o", "best", "ticks", "last_round", "last_commits", "ev_value", "ev_a", "ev_b",
-        "accepts", "descents", "held", "first_value", "gain_descent", "gain_ls")
+        "accepts", "descents", "held", "first_value", "gain_descent", "gain_ls", "steps")
 
 
 @pytest.fixture(scope="module")

@@ -213,3 +213,21 @@ def test_maxcut_acceptance_is_strict():
         lambda k: oracle.params(problem=oracle.MAXCUT, alpha=0.05, momentum=0.8, rho=0.5, t_gs=6,
                                 descent_cap=40, init_kind=1, sigma=0.2, seed=60 + k), 600)
     assert _check_strict(events) >= 5
+
+
+# ---------------------------------------------------------------- step count
+def test_steps_count_the_ticks_that_ran_a_gradient_step():
+    """`steps` grows by one exactly on the ticks whose round is a descent step
+    (last_round == -1); with repair and local search off every tick steps."""
+    G = mi.erdos_renyi(40, 0.15, 1)
+    g = oracle.Graph(G)
+    tr = oracle.Trajectory(g, oracle.params(t_gs=3, descent_cap=20, seed=5), 0)
+    for _ in range(400):
+        before = tr.state["steps"]
+        tr.run(1)
+        st = tr.state
+        assert st["steps"] - before == (1 if st["last_round"] == -1 else 0)
+    assert 0 < st["steps"] < st["ticks"]
+    tr = oracle.Trajectory(g, oracle.params(t_gs=3, descent_cap=20, seed=5, local_search=0, repair=0), 0)
+    tr.run(300)
+    assert tr.state["steps"] == tr.state["ticks"] == 300
