@@ -411,6 +411,12 @@ def step_kernel_traffic(workload, x_dtype, variant):
 
 
 INT64_MIN = -(1 << 63)
+_T0 = time.perf_counter()
+
+
+def progress(what):
+    """One line per bench phase on stderr (seconds since start)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {what}", file=sys.stderr, flush=True)
 
 
 def per_graph_nnz(G):
@@ -646,8 +652,10 @@ def gpu_arm(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     cpu_leg = rank == 0 and world == 1 and not args.no_cpu
 
+    progress(f"{args.workload}: timed ticks")
     main = measure_solver(mq, G, pkw, xd, vd, args.steps, args.warmup, autotune=not args.no_autotune,
                           clocks_of=local, barrier=barrier, probe=8 if cpu_leg else 0)
+    progress("end to end")
     ms, value = aggregate_ranks(main["ms"], main["stepped_edge_updates"], dist, "cuda")
     _, value_all = aggregate_ranks(main["ms"], main["all_edge_updates"], dist, "cuda")
     step_avg_ms = main["phase_ms"]["step"] / args.steps
@@ -709,6 +717,7 @@ def gpu_arm(args):
     cpu = None
     objective_f64 = None
     if cpu_leg:
+        progress("oracle sample")
         cpu = oracle_sample(G, wl, xd, vd, target_s=12.0, pool_k=args.pool_k, objective=OBJECTIVES[args.objective])
         objective_f64 = objective_error(G, wl, OBJECTIVES[args.objective], main.get("objective_probe", {}))
 
@@ -824,8 +833,11 @@ def quality_vs_single(mq, G, pkw, xd, vd, xname, *, ticks):
     import torch
     B = pkw["batch"]
     out = {"ticks": ticks, "graph": "member graph 0 of the batch"}
-    for label, gg, x_d, v_d in ((f"batched_{xname}", G, xd, vd), ("batched_f32", G, 0, 0),
-                                ("single_instance_f32", G.subgraph(0), 0, 0)):
+    runs = [(f"batched_{xname}", G, xd, vd)]
+    if xd != 0 and vd != 0:
+        runs.append((f"batched_{xname}_vf32", G, xd, 0))
+    runs += [("batched_f32", G, 0, 0), ("single_instance_f32", G.subgraph(0), 0, 0)]
+    for label, gg, x_d, v_d in runs:
         g = mq.Graph(gg)
         s = mq.Solver(g, mq.params(x_dtype=x_d, v_dtype=v_d, **pkw))
         s.run(10)
@@ -859,6 +871,7 @@ def paper_er_record(mq, ticks, rank):
     out = {"ticks": ticks, "note": "seeded synthetic ER graphs of the paper's (n, d), tick budget; the paper's "
                                    "numbers come from its own graphs and a time budget: context only"}
     for name in PAPER_ER:
+        progress(f"  {name}")
         wl = WORKLOADS[name]
         G = make_graph(name)
         B = wl["batch"]
@@ -882,23 +895,32 @@ def default_line_subrecords(mq, G, wl, pkw, xd, vd, xname, *, local, rank, cpu):
     """Sub-records of the default bench line: steady state, batched against
     single instance, the other configurations (large MIS, MaxCut, autograd)
     and the paper-shaped ER workloads."""
-    out = {"steady_state": steady_state(mq, G, pkw, xd, vd, warm=400, repeats=10, ticks=100, local=local),
-           "quality_vs_single_instance": quality_vs_single(mq, G, pkw, xd, vd, xname, ticks=1000)}
+    progress("steady state")
+    out = {"steady_state": steady_state(mq, G, pkw, xd, vd, warm=400, repeats=10, ticks=100, local=local)}
+    progress("batched against single instance")
+    out["quality_vs_single_instance"] = quality_vs_single(mq, G, pkw, xd, vd, xname, ticks=1000)
     cfg = {}
     for name, xs, vs in (("maxcut_regular", "bf16", "bf16"), ("maxcut_regular", "bf16", "f32"),
                          ("maxcut_regular_signed", "bf16", "bf16")):
+        progress(f"{name} x {xs} V {vs}")
         cfg[f"{name}_{xs}_v{vs}"] = solver_config_record(mq, name, xs, vs, 20, 5, 2000, local=local, rank=rank,
                                                          cpu=cpu, oracle_ticks=400)
+    progress("mis_scale graph")
     Gs = make_graph("mis_scale")
-    for xs in ("f16", "f32"):
-        cfg[f"mis_scale_{xs}"] = solver_config_record(mq, "mis_scale", xs, xs, 20, 5, 100, local=local, rank=rank,
-                                                      cpu=cpu and xs == "f16", G=Gs, oracle_ticks=2)
+    for xs, vs in (("f16", "f16"), ("f16", "f32"), ("f32", "f32")):
+        progress(f"mis_scale x {xs} V {vs}")
+        cfg[f"mis_scale_{xs}_v{vs}"] = solver_config_record(mq, "mis_scale", xs, vs, 20, 5, 100, local=local,
+                                                            rank=rank, cpu=cpu and vs == "f16", G=Gs, oracle_ticks=2)
     del Gs
+    progress("autograd")
     cfg["autograd_powerlaw_f32"] = autograd_measure(mq, 20, 5, local=local, rank=rank, dist=None,
                                                     cpu=cpu, cpu_target_s=6.0)
     out["configs"] = cfg
+    progress("paper-shaped ER")
     out["paper_er"] = paper_er_record(mq, 5000, rank)
+    progress("App. B")
     out["app_b"] = app_b_record(mq, rank, cpu)
+    progress("sub-records done")
     return out
 
 
@@ -950,8 +972,13 @@ def app_b_record(mq, rank, cpu, steps=2000):
     for dens in (0.66, 0.017):
         G = mi.pack([mi.erdos_renyi(100, dens, 500 + k) for k in range(10)])
         rng = np.random.default_rng(1000 * rank + 3)
-        c = rng.uniform(-1.0, 1.0, size=(G.num_graphs, B)).astype(np.float32)
-        x_c = np.repeat(c, 100, axis=0)  # x = c 1 on each graph, one c per trajectory
+        # x = c 1 on each graph, one c per trajectory; c = +-k/16 so that every
+        # float32 row sum of c is exact and c 1 is exactly stationary for f_L
+        # (Prop. 3.2); a c with more mantissa bits leaves rounding residues in
+        # L x that the step amplifies
+        c = (rng.integers(1, 16, size=(G.num_graphs, B)) * rng.choice([-1.0, 1.0], size=(G.num_graphs, B)) /
+             16.0).astype(np.float32)
+        x_c = np.repeat(c, 100, axis=0)
         x_pm = np.where(rng.random((G.n, B)) < 0.5, -1.0, 1.0).astype(np.float32)
         for label, x0, paper in (("table3_stationary_c1", x_c, {"fl": [0, 0], "fp": [0, 47.2], "fb": [0, 51.1]}),
                                  ("table4_one_flip_repairable", x_pm,

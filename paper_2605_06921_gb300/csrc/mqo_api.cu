@@ -724,10 +724,13 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     s->step_smem_max = (B >= 32 && need <= kStepSmemLimit) ? need : 0;
     s->step_smem = (generic || staged) ? 0 : s->step_smem_max;
     if (staged_possible(B, p->x_dtype, p->v_dtype)) {
-      const mqo_solver_s::SliceSet ss = slice_set(s, kDefaultSliceKB);
-      if (ss.count > 0) {
-        s->staged_ok = true;
-        use_slices(s, ss);
+      // the smallest slice capacity from the default up that holds every row
+      for (int kb = kDefaultSliceKB; kb <= 128 && !s->staged_ok; kb *= 2) {
+        const mqo_solver_s::SliceSet ss = slice_set(s, kb);
+        if (ss.count > 0) {
+          s->staged_ok = true;
+          use_slices(s, ss);
+        }
       }
     }
     s->S.step_staged = (s->staged_ok && !generic) ? 1 : 0;
@@ -1275,7 +1278,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
           if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc, 0, 0});
         }
         if (s->staged_ok)
-          for (int kb : {16, 32, 64}) {
+          for (int kb : {16, 32, 64, 128}) {
             if (slice_set(s, kb).count <= 0) continue;
             for (int v : {2, 4, 8})
               if (staged_vec_ok(B, S.p.x_dtype, v)) plans.push_back({0, v, 0, dc, 1, kb});

@@ -282,12 +282,17 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
       if (a.g.w) w = a.g.w[j + lane];
     }
     unsigned char* dst = buf + (size_t)slot * PIPE * ROWB;
-    for (int k = lane; k < cnt * PER; k += 32) {
-      const int e = k / PER;
-      const int piece = k - e * PER;
+    // the trip count is the same for every lane (every lane must reach the
+    // full-warp shuffle); only the copy is predicated
+    const int total = cnt * PER;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+      const int k = k0 + lane;
+      const int e = min(k / PER, 31);
+      const int piece = k - (k / PER) * PER;
       const int32_t ue = __shfl_sync(0xffffffffu, c, e);
-      fb_cp_async16(dst + e * ROWB + piece * 16,
-                    reinterpret_cast<const unsigned char*>(a.X + (int64_t)ue * B) + piece * 16);
+      if (k < total)
+        fb_cp_async16(dst + e * ROWB + piece * 16,
+                      reinterpret_cast<const unsigned char*>(a.X + (int64_t)ue * B) + piece * 16);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };

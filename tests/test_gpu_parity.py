@@ -182,11 +182,23 @@ def test_staged_step_kernel(mq, monkeypatch, problem, weighted, B, xd, vd):
     assert s.info()["step_kernel"] == "staged"
 
 
-def test_staged_step_kernel_falls_back_on_long_rows(mq, monkeypatch):
-    """a row whose neighbour rows of x exceed one slice (a star of 300 leaves,
-    256-byte rows: 75 KB): the plain global-memory kernel takes the step"""
+def test_staged_step_kernel_grows_the_slice_for_long_rows(mq, monkeypatch):
+    """a star of 200 leaves with 256-byte rows of x (50 KB of neighbour rows):
+    the staged kernel takes 64 KB slices"""
     monkeypatch.setenv("MQO_STEP_KERNEL", "staged")
-    star = mi.from_edges(301, np.zeros(300, int), np.arange(1, 301))
+    star = mi.from_edges(201, np.zeros(200, int), np.arange(1, 201))
+    G = mi.pack([star, mi.erdos_renyi(80, 0.1, 5)])
+    p = mq.params(problem=1, batch=128, x_dtype=1, alpha=0.05, momentum=0.5, seed=6)
+    s = _plain_steps(mq, G, p, 6)
+    assert s.info()["step_kernel"] == "staged" and s.info()["slice_kb"] == 64
+
+
+def test_staged_step_kernel_falls_back_on_long_rows(mq, monkeypatch):
+    """a row whose neighbour rows of x exceed the largest slice (a star of 600
+    leaves, 256-byte rows: 150 KB against 128 KB): the plain global-memory
+    kernel takes the step"""
+    monkeypatch.setenv("MQO_STEP_KERNEL", "staged")
+    star = mi.from_edges(601, np.zeros(600, int), np.arange(1, 601))
     G = mi.pack([star, mi.erdos_renyi(80, 0.1, 4)])
     p = mq.params(problem=1, batch=128, x_dtype=1, alpha=0.05, momentum=0.5, seed=4)
     s = _plain_steps(mq, G, p, 6)
