@@ -92,6 +92,9 @@ AUTOGRAD = dict(desc="f_B autograd: Chung-Lu power law (exponent 2.5, mean degre
                      "forward + backward + projected momentum step", batch=64, lambda_=0.001, lr=0.001, momentum=0.9)
 
 
+MIS_SCALE_NODES = [10_000_000]  # --nodes overrides it (smaller cases for profiling)
+
+
 def make_graph(name):
     if name == "mis_batched":
         return mi.workload_mis_batched()
@@ -100,7 +103,7 @@ def make_graph(name):
     if name == "maxcut_regular_signed":
         return mi.workload_maxcut_regular(signed=True)
     if name == "mis_scale":
-        return mi.workload_mis_scale()
+        return mi.workload_mis_scale(n=MIS_SCALE_NODES[0])
     if name.startswith("er_"):
         n, d = (int(t) for t in name.split("_")[-2:])
         return mi.workload_er_table(n, float(d))
@@ -1265,6 +1268,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="same as --no-sub")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--nodes", type=int, default=None, help="mis_scale: nodes of the ER graph (default 1e7)")
     ap.add_argument("--no-sub", action="store_true",
                     help="default workload: leave out the sub-records (steady state, other configurations)")
     ap.add_argument("--pool-k", type=int, default=0, help="pmQO pool of K sets per graph (0: Alg. 1/2)")
@@ -1279,6 +1283,8 @@ def main():
         args.warmup = 3
     if args.no_compare:
         args.no_sub = True
+    if args.nodes:
+        MIS_SCALE_NODES[0] = args.nodes
     if args.rho is not None:
         WORKLOADS[args.workload]["rho"] = args.rho
     if args.rho_sweep:

@@ -157,7 +157,7 @@ bool build_slices(const mqo_graph_s* g, int32_t rows, int32_t cols, std::vector<
         c += d;
         v1 += 1;
       }
-      out.push_back(Slice{item.g, it, v0, v1});
+      out.push_back(Slice{item.g, it, v0, v1, g->h_rp[(size_t)v0], g->h_rp[(size_t)v1], 0, 0});
       v0 = v1;
     }
   }
@@ -427,7 +427,32 @@ mqo_status build_heavy_plan(mqo_graph g) {
     }
   }
   hfirst.push_back((int32_t)hrow.size());
-  const size_t total = light.size() + 3 * hrow.size() + hrows.size() + hfirst.size();
+  // segments of consecutive light rows, cut before a heavy row or once a
+  // segment holds kFbSegEntries entries
+  std::vector<int32_t> segs;
+  {
+    int64_t r0 = -1;
+    auto close = [&](int64_t r1) {
+      if (r0 >= 0 && r1 > r0) {
+        segs.push_back((int32_t)r0);
+        segs.push_back((int32_t)r1);
+        segs.push_back(g->h_rp[(size_t)r0]);
+        segs.push_back(g->h_rp[(size_t)r1]);
+      }
+      r0 = -1;
+    };
+    for (int64_t v = 0; v < g->n; ++v) {
+      const int32_t d = g->h_rp[(size_t)v + 1] - g->h_rp[(size_t)v];
+      if (d > kSplit) {
+        close(v);
+        continue;
+      }
+      if (r0 < 0) r0 = v;
+      if (g->h_rp[(size_t)v + 1] - g->h_rp[(size_t)r0] >= kFbSegEntries) close(v + 1);
+    }
+    close(g->n);
+  }
+  const size_t total = light.size() + 3 * hrow.size() + hrows.size() + hfirst.size() + segs.size() + 4;
   mqo_status st = dalloc(&g->d_hp, total, nullptr);
   if (st != MQO_OK) return st;
   int32_t* p = g->d_hp;
@@ -446,6 +471,10 @@ mqo_status build_heavy_plan(mqo_graph g) {
   g->hp.heavy_rows = put(hrows);
   g->hp.heavy_first = put(hfirst);
   g->hp.num_heavy = (int32_t)hrows.size();
+  // the segment records are int4: start them on a 16-byte boundary
+  while (((uintptr_t)p & 15u) != 0) ++p;
+  g->hp.segs = reinterpret_cast<const int4*>(put(segs));
+  g->hp.num_segs = (int32_t)(segs.size() / 4);
   CKG(cudaGetLastError());
   g->hp_built = true;
   return MQO_OK;

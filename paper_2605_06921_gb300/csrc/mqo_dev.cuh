@@ -107,11 +107,11 @@ struct Item {
   int32_t g, v0, v1, pad;
 };
 
-// A node range [v0, v1) inside work item `it` of member graph g: the unit of
-// the staged-gather step kernel (at most slice_rows rows whose CSR rows hold
-// at most slice_cols entries together).
-struct Slice {
-  int32_t g, it, v0, v1;
+// A node range [v0, v1) inside work item `it` of member graph g, CSR
+// entries [j0, j1): the unit of the staged-gather step kernels (at most
+// slice_rows rows whose CSR rows hold at most slice_cols entries together).
+struct __align__(16) Slice {
+  int32_t g, it, v0, v1, j0, j1, pad0, pad1;
 };
 
 struct GraphDev {

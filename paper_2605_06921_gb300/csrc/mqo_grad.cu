@@ -198,15 +198,10 @@ __global__ void __launch_bounds__(256) k_fb_heavy(FbArgs a) {
   }
 }
 
-// ---------------------------------------------------------------- pipelined units
-// B >= 32: one warp is one row group (lane l owns columns l*VEC ..).  Each
-// warp walks its units (light rows and 512-entry chunks, as k_fb_units) as
-// one stream of batches of at most `pipe` CSR entries (pipe * B * 4 bytes =
-// 4 KB): the neighbour rows of x of the next batch are copied into the
-// warp's other shared-memory buffer with cp.async while the current batch
-// is summed, so every warp keeps a batch of gathers in flight across unit
-// boundaries.  The sums run over each unit's entries in CSR order, exactly
-// as in k_fb_units.
+// ---------------------------------------------------------------- pipelined rows
+// B >= 32: one warp is one row group (lane l owns columns l*VEC ..); batches
+// of at most PIPE CSR entries (PIPE * B * 4 bytes = 4 KB) are copied into the
+// warp's two shared-memory buffers with cp.async, one batch ahead.
 constexpr int kFbPipeBytes = 4096;  // gathered bytes per batch and warp
 constexpr int kFbPipeThreads = 256;
 
@@ -222,47 +217,36 @@ __device__ __forceinline__ void fb_cp_async16(void* smem_dst, const void* gsrc) 
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 
-struct FbUnit {
-  int64_t row;
-  int32_t j0, j1;
-  bool whole, valid;
+// ---------------------------------------------------------------- segment stream
+// B >= 32, light rows: warp w walks segments w, w + W, ... (consecutive
+// light rows, their entries contiguous in CSR) as one stream of batches of
+// at most PIPE entries; a batch never spans two segments.  Three positions
+// move along the stream: the column indices (and weights) of batch i+2 are
+// loaded into lane registers, the neighbour rows of batch i+1 are copied
+// into shared memory with cp.async (from indices loaded one batch earlier),
+// and batch i is summed.  Row ends come from a window of 32 row pointers
+// held across the lanes; every row is summed in CSR order and emitted as in
+// k_fb_units (gradient, objective), so the results equal k_fb_units's.
+struct FbBatch {
+  int64_t seg;  // segment index (>= num_segs: past the end)
+  int4 d;       // {first row, end row, first entry, end entry} of the segment
+  int32_t jb;   // first entry of the batch
 };
 
-__device__ __forceinline__ FbUnit fb_unit(const FbArgs& a, int64_t u, int64_t nunits) {
-  FbUnit r;
-  r.valid = u < nunits;
-  r.whole = true;
-  r.row = 0;
-  r.j0 = r.j1 = 0;
-  if (!r.valid) return r;
-  if (u < a.hp.num_light) {
-    r.row = a.hp.light_rows[u];
-    r.j0 = a.g.row_ptr[r.row];
-    r.j1 = a.g.row_ptr[r.row + 1];
-  } else {
-    const int64_t c = u - a.hp.num_light;
-    r.whole = false;
-    r.row = a.hp.heavy_row[c];
-    r.j0 = a.hp.heavy_j0[c];
-    r.j1 = a.hp.heavy_j1[c];
-  }
-  return r;
-}
-
 template <int VEC>
-__global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
+__global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
   extern __shared__ __align__(16) unsigned char smem_fb[];
   __shared__ double s_obj[256];
   constexpr int B = 32 * VEC;
   constexpr int ROWB = B * 4;
   constexpr int PIPE = kFbPipeBytes / ROWB < 32 ? kFbPipeBytes / ROWB : 32;
-  constexpr int PER = ROWB / 16;  // 16-byte pieces of one row
+  constexpr int PER = ROWB / 16;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int b0 = lane * VEC;
   unsigned char* buf = smem_fb + (size_t)warp * 2 * PIPE * ROWB;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t nunits = (int64_t)a.hp.num_light + a.hp.num_chunks;
+  const int64_t nseg = a.hp.num_segs;
   const bool want_obj = a.obj != nullptr;
   for (int i = threadIdx.x; i < B; i += blockDim.x) s_obj[i] = 0.0;
   __syncthreads();
@@ -272,20 +256,35 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
   for (int e = 0; e < VEC; ++e) { objf[e] = 0.0f; objd[e] = 0.0; }
   int pending = 0;
 
-  // copy the rows of entries [j, j + cnt) into buffer `slot`; lane e < cnt
-  // returns entry j+e's column index and weight in c / w
-  auto issue = [&](int32_t j, int cnt, int slot, int32_t& c, int& w) {
+  auto first = [&](int64_t sg) {
+    FbBatch x;
+    x.seg = sg;
+    x.d = sg < nseg ? a.hp.segs[sg] : make_int4(0, 0, 0, 0);
+    x.jb = x.d.z;
+    return x;
+  };
+  auto next = [&](const FbBatch& x) {
+    if (x.jb + PIPE < x.d.w) {
+      FbBatch y = x;
+      y.jb = x.jb + PIPE;
+      return y;
+    }
+    return first(x.seg + W);
+  };
+  auto count = [&](const FbBatch& x) { return x.seg < nseg ? min(PIPE, x.d.w - x.jb) : 0; };
+  // lane e < count: the column index and weight of entry jb + e
+  auto load_idx = [&](const FbBatch& x, int32_t& c, int& w) {
     c = 0;
     w = 1;
-    if (lane < cnt) {
-      c = __ldcs(a.g.col + j + lane);
-      if (a.g.w) w = a.g.w[j + lane];
+    if (lane < count(x)) {
+      c = __ldcs(a.g.col + x.jb + lane);
+      if (a.g.w) w = a.g.w[x.jb + lane];
     }
+  };
+  auto issue = [&](const FbBatch& x, int32_t c, int slot) {
     unsigned char* dst = buf + (size_t)slot * PIPE * ROWB;
-    // the trip count is the same for every lane (every lane must reach the
-    // full-warp shuffle); only the copy is predicated
-    const int total = cnt * PER;
-    for (int k0 = 0; k0 < total; k0 += 32) {
+    const int total = count(x) * PER;
+    for (int k0 = 0; k0 < total; k0 += 32) {  // same trip count on every lane
       const int k = k0 + lane;
       const int e = min(k / PER, 31);
       const int piece = k - (k / PER) * PER;
@@ -297,33 +296,83 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
 
-  int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  FbUnit cur = fb_unit(a, u, nunits);
-  int32_t jb = cur.j0;  // first entry of the current batch
-  int slot = 0;
-  int32_t cidx;
-  int wcur, wnext;
-  issue(jb, cur.valid ? min(PIPE, cur.j1 - jb) : 0, slot, cidx, wcur);
+  // row state of the batch being summed
+  int32_t row = 0, rbase = 0, rend_lane = 0, row_end = 0, seg_end_row = 0;
   float acc[VEC];
+  float xo[VEC];  // own row of x (objective)
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
-  while (cur.valid) {
-    // the batch after this one: the rest of this unit, or the next unit
-    FbUnit nxt = cur;
-    int64_t un = u;
-    int32_t jn = jb + PIPE;
-    if (jn >= cur.j1) {
-      un = u + W;
-      nxt = fb_unit(a, un, nunits);
-      jn = nxt.j0;
+  for (int e = 0; e < VEC; ++e) acc[e] = 0.0f, xo[e] = 0.0f;
+  auto window = [&](int32_t r) {  // lane i: end entry of row r + i
+    rbase = r;
+    rend_lane = r + lane < seg_end_row ? a.g.row_ptr[r + lane + 1] : 0x7fffffff;
+  };
+  auto start_row = [&](int32_t r) {
+    row = r;
+    if (r - rbase >= 32) window(r);
+    row_end = __shfl_sync(0xffffffffu, rend_lane, r - rbase);
+    if (want_obj && r < seg_end_row) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) xo[e] = a.X[(int64_t)r * B + b0 + e];
     }
-    issue(jn, nxt.valid ? min(PIPE, nxt.j1 - jn) : 0, slot ^ 1, cidx, wnext);
+  };
+  auto emit = [&]() {
+    if (a.G) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float tt = 2.0f * acc[e];
+        float gr = -a.lambda_ - tt;
+        if (a.gout) gr = a.gout[b0 + e] * gr;
+        __stcs(a.G + (int64_t)row * B + b0 + e, gr);
+      }
+    }
+    if (want_obj) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float t1 = a.lambda_ * xo[e];
+        const float t2 = xo[e] * acc[e];
+        objf[e] = objf[e] - t1;
+        objf[e] = objf[e] - t2;
+      }
+      if (++pending == 16) flush_obj<VEC>(objf, objd, pending);
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.0f;
+  };
+
+  FbBatch cur = first((int64_t)blockIdx.x * (blockDim.x >> 5) + warp);
+  FbBatch nx1 = next(cur);
+  FbBatch nx2 = next(nx1);
+  int32_t c_cur, c1, c2;
+  int w_cur, w1, w2;
+  load_idx(cur, c_cur, w_cur);
+  load_idx(nx1, c1, w1);
+  issue(cur, c_cur, 0);
+  load_idx(nx2, c2, w2);
+  int slot = 0;
+  while (cur.seg < nseg) {
+    // rows of batch i+1 out (indices loaded one batch ago), indices of
+    // batch i+2 in; then wait for batch i
+    issue(nx1, c1, slot ^ 1);
+    FbBatch nx3 = next(nx2);
+    int32_t c3;
+    int w3;
+    load_idx(nx3, c3, w3);
+    if (cur.jb == cur.d.z) {  // the first batch of a segment
+      seg_end_row = cur.d.y;
+      window(cur.d.x);
+      start_row(cur.d.x);
+    }
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncwarp();
-    const int cnt = min(PIPE, cur.j1 - jb);
+    const int cnt = count(cur);
     const unsigned char* src = buf + (size_t)slot * PIPE * ROWB + b0 * 4;
     for (int e = 0; e < cnt; ++e) {
-      const int w = __shfl_sync(0xffffffffu, wcur, e);
+      const int32_t j = cur.jb + e;
+      while (j >= row_end) {  // rows that end before entry j (empty rows too)
+        emit();
+        start_row(row + 1);
+      }
+      const int w = __shfl_sync(0xffffffffu, w_cur, e);
       float f[VEC];
       if constexpr (VEC == 1) {
         f[0] = *reinterpret_cast<const float*>(src + e * ROWB);
@@ -345,23 +394,21 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
       for (int q = 0; q < VEC; ++q) acc[q] = w >= 0 ? acc[q] + f[q] : acc[q] - f[q];
     }
     __syncwarp();
-    if (jb + PIPE >= cur.j1) {  // the unit is complete
-      if (cur.whole) {
-        FbOut<VEC>::emit(cur.row, acc, a.X, B, b0, a.lambda_, a.gout, a.G, want_obj, objf);
-        if (++pending == 16) flush_obj<VEC>(objf, objd, pending);
-      } else {
-        const int64_t c = u - a.hp.num_light;
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) a.scratch[c * B + b0 + q] = acc[q];
+    if (cur.jb + PIPE >= cur.d.w) {  // the segment's last batch: its remaining rows
+      while (row < seg_end_row) {
+        emit();
+        start_row(row + 1);
       }
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) acc[q] = 0.0f;
     }
-    cur = nxt;
-    u = un;
-    jb = jn;
+    cur = nx1;
+    nx1 = nx2;
+    nx2 = nx3;
+    c1 = c2;
+    w_cur = w1;
+    w1 = w2;
+    c2 = c3;
+    w2 = w3;
     slot ^= 1;
-    wcur = wnext;
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (want_obj) {
@@ -377,22 +424,29 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_pipe(FbArgs a) {
 
 template <int VEC>
 static cudaError_t launch_fb_vec(const FbArgs& a, int grid, cudaStream_t s) {
-  if ((int64_t)a.hp.num_light + a.hp.num_chunks > 0) {
-    if (a.B == 32 * VEC && fb_pipe_enabled()) {
+  if (a.B == 32 * VEC && fb_pipe_enabled()) {
+    // light rows: the segment stream; heavy rows: their 512-entry chunks by
+    // the unit kernel, then the chunk sums
+    if (a.hp.num_segs > 0) {
       constexpr int ROWB = 32 * VEC * 4;
       constexpr int PIPE = kFbPipeBytes / ROWB < 32 ? kFbPipeBytes / ROWB : 32;
       const size_t smem = (size_t)(kFbPipeThreads / 32) * 2 * PIPE * ROWB;
-      cudaError_t e = cudaFuncSetAttribute(k_fb_pipe<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = cudaFuncSetAttribute(k_fb_seg<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      // one wave: the resident CTAs of every SM (each warp strides over the units)
+      // one wave: the resident CTAs of every SM (each warp strides over the segments)
       int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fb_pipe<VEC>, kFbPipeThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fb_seg<VEC>, kFbPipeThreads, smem);
       if (e != cudaSuccess) return e;
       const int pgrid = std::max(1, std::min(grid, per_sm * (grid / 8)));
-      k_fb_pipe<VEC><<<pgrid, kFbPipeThreads, smem, s>>>(a);
-    } else {
-      k_fb_units<VEC><<<grid, 256, 0, s>>>(a);
+      k_fb_seg<VEC><<<pgrid, kFbPipeThreads, smem, s>>>(a);
     }
+    if (a.hp.num_chunks > 0) {
+      FbArgs c = a;
+      c.hp.num_light = 0;  // units = the chunks of heavy rows only
+      k_fb_units<VEC><<<grid, 256, 0, s>>>(c);
+    }
+  } else if ((int64_t)a.hp.num_light + a.hp.num_chunks > 0) {
+    k_fb_units<VEC><<<grid, 256, 0, s>>>(a);
   }
   if (a.hp.num_heavy > 0) k_fb_heavy<VEC><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();

@@ -54,7 +54,12 @@ struct HeavyPlan {
   const int32_t* heavy_rows;  // distinct heavy rows
   const int32_t* heavy_first; // per heavy row: first chunk
   int32_t num_heavy;
+  // light rows in segments of consecutive rows (no heavy row inside) of
+  // about kFbSegEntries entries: {first row, end row, first entry, end entry}
+  const int4* segs;
+  int32_t num_segs;
 };
+constexpr int kFbSegEntries = 512;
 
 cudaError_t launch_fb(const GraphDev& g, const HeavyPlan& hp, const float* X, int B, float lambda_,
                       const float* gout, float* G, double* obj, float* scratch, int grid, cudaStream_t stream);

@@ -351,7 +351,8 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   if (smem == 0 && S.step_staged) {
     // staged-gather kernel: one CTA per slice
     const int vec = S.step_vec > 0 ? S.step_vec : default_staged_vec(S.B, xd);
-    const size_t qs = staged_layout(S.B, xd == DT_F32 ? 4 : 2, vd == DT_F32 ? 4 : 2, S.slice_cols, S.slice_rows,
+    const int sx = xd == DT_F32 ? 4 : 2, sv = vd == DT_F32 ? 4 : 2;
+    const size_t qs = staged_layout(S.B, sx, sv, S.slice_cols, S.slice_rows,
                                     S.g.w != nullptr && S.p.problem != PROB_MIS)
                           .total;
     return launch_step_staged(a, vec, xd, vd, qs, stream);

@@ -28,7 +28,6 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
 // VEC elements of T at p (aligned) as floats
 template <typename T, int VEC>
 __device__ __forceinline__ void unpack_row(const unsigned char* p, float* f) {

@@ -165,7 +165,8 @@ def test_staged_step_kernel(mq, monkeypatch, problem, weighted, B, xd, vd):
     """the staged-gather step kernel (the default for graphs too large for
     shared memory) on small graphs; with 256-byte rows of x (B = 128 in
     16-bit, B = 64 in float32) every work item spans many slices"""
-    monkeypatch.setenv("MQO_STEP_KERNEL", "staged")
+    mode = "staged"
+    monkeypatch.setenv("MQO_STEP_KERNEL", mode)
     monkeypatch.setenv("MQO_DISC_KERNEL", "pairs")
     G = small_batch(3, 60, 300, 0.05, seed=B + xd)
     if weighted:
@@ -173,13 +174,13 @@ def test_staged_step_kernel(mq, monkeypatch, problem, weighted, B, xd, vd):
     p = mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, alpha=0.8 if problem == 0 else 0.05,
                   momentum=0.5, seed=B + 11)
     s = _plain_steps(mq, G, p, 8)
-    assert s.info()["step_kernel"] == "staged" and s.info()["slice_kb"] == 32
+    assert s.info()["step_kernel"] == mode and s.info()["slice_kb"] == 32
     G = small_batch(2, 30, 60, 0.15, seed=B + 9)
     if weighted:
         G = signed(G, B + 1)
     s, _ = _machine(mq, G, mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, t_gs=3, descent_cap=20,
                                      seed=9), 150)
-    assert s.info()["step_kernel"] == "staged"
+    assert s.info()["step_kernel"] == mode
 
 
 def test_staged_step_kernel_grows_the_slice_for_long_rows(mq, monkeypatch):
