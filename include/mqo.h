@@ -298,8 +298,11 @@ MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
  * lane, twice the rows per warp), bit 3 = the global-memory step runs as the
  * staged-gather kernel (each CTA copies every neighbour row of x of a slice
  * of rows into shared memory before summing), bits 4..7 = trajectories per
- * lane of a global-memory step kernel (0 with bit 0), bits 8.. = KB of
- * gathered rows of x per staged slice (0 without bit 3); *smem_bytes = the
+ * lane of a global-memory step kernel (0 with bit 0), bits 8..15 = KB of
+ * gathered rows of x per staged slice (0 without bit 3), bit 16 = the
+ * shared-memory step kernel reads 16-bit member-local column indices (kept
+ * by the graph when every member graph has fewer than 65535 nodes, 2 bytes
+ * per entry of device memory); *smem_bytes = the
  * shared-memory step kernel's dynamic shared memory per CTA; *items = work
  * items (node ranges of at most 256 nodes); *replicas = counter replicas per
  * trajectory.

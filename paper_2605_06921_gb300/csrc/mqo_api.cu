@@ -59,6 +59,7 @@ struct mqo_graph_s {
   int32_t* d_dmax = nullptr;
   Item* d_items = nullptr;
   int32_t* d_order = nullptr;
+  uint16_t* d_col16 = nullptr;  // member-local column indices (every member graph below 65536 nodes)
   int32_t num_items = 0;
   std::vector<int32_t> h_rp;
   std::vector<int32_t> h_off;
@@ -87,6 +88,7 @@ struct mqo_graph_s {
     g.dmax = d_dmax;
     g.items = d_items;
     g.order = d_order;
+    g.col16 = d_col16;
     g.num_items = num_items;
     return g;
   }
@@ -405,6 +407,18 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
       return cleanup(st);
     }
   }
+  // 16-bit member-local column indices for the shared-memory step kernel
+  // when every member graph (and its zero dummy row) fits in them
+  if (on_gpu && nnz > 0) {
+    int32_t max_ng = 0;
+    for (int32_t k = 0; k < G; ++k) max_ng = std::max<int32_t>(max_ng, off32[(size_t)k + 1] - off32[(size_t)k]);
+    if (max_ng < 65535) {
+      if ((st = dalloc(&g->d_col16, (size_t)nnz, nullptr)) != MQO_OK) return cleanup(st);
+      e = launch_col16(g->dev(), g->d_col16, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return cleanup(fail(MQO_ECUDA, "graph upload: %s", cudaGetErrorString(e)));
+    }
+  }
   *out = g;
   return MQO_OK;
 }
@@ -644,6 +658,7 @@ mqo_status mqo_graph_destroy(mqo_graph g) {
   cudaFree(g->d_dmax);
   cudaFree(g->d_items);
   cudaFree(g->d_order);
+  cudaFree(g->d_col16);
   cudaFree(g->d_hp);
   cudaFree(g->d_scratch);
   delete g;
@@ -763,6 +778,10 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
       }
     }
     s->S.step_staged = (s->staged_ok && !generic) ? 1 : 0;
+    // 16-bit column indices in the shared-memory step kernel where the graph
+    // has them (MQO_COL16=0: the 32-bit ones)
+    const char* c16 = getenv("MQO_COL16");
+    s->S.step_c16 = g->d_col16 != nullptr && !(c16 && strcmp(c16, "0") == 0) ? 1 : 0;
     // MQO_STEP_KERNEL=wide: the shared-memory kernel with 16-byte lanes
     s->S.step_wide = force && strcmp(force, "wide") == 0 && step_wide_possible(B, p->x_dtype) ? 1 : 0;
     // The fused per-graph discrete kernel runs one CTA per member graph, so
@@ -1078,7 +1097,7 @@ mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_byt
   if (step_kernel)
     *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0) |
                    (s->step_smem > 0 && s->S.step_wide ? 4 : 0) | (staged ? 8 : 0) | (vec << 4) |
-                   ((staged ? slice_kb(s) : 0) << 8);
+                   ((staged ? slice_kb(s) : 0) << 8) | ((s->step_smem > 0 && s->S.step_c16) ? (1 << 16) : 0);
   if (smem_bytes) *smem_bytes = (int64_t)s->step_smem;
   if (items) *items = s->S.g.num_items;
   if (replicas) *replicas = s->S.R;
@@ -1288,6 +1307,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     size_t disc_smem;
     int staged;   // staged-gather step kernel
     int slice_kb; // its slice capacity
+    int c16;      // shared-memory step kernel with 16-bit column indices
   };
   std::vector<Plan> plans;
   std::vector<size_t> steps = {0};
@@ -1298,23 +1318,26 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
   for (size_t st : steps)
     for (size_t dc : discs) {
       if (st > 0) {
-        plans.push_back({st, 0, 0, dc, 0, 0});
-        if (wide_ok) plans.push_back({st, 0, 1, dc, 0, 0});
+        for (int c16 : {0, 1}) {
+          if (c16 && !s->g->d_col16) continue;
+          plans.push_back({st, 0, 0, dc, 0, 0, c16});
+          if (wide_ok) plans.push_back({st, 0, 1, dc, 0, 0, c16});
+        }
       } else {
         for (int v : {1, 2, 4, 8}) {
           // 16-byte lanes (8 trajectories) only for 16-bit x and momentum
           if (v == 8 && (S.p.x_dtype == DT_F32 || S.p.v_dtype == DT_F32)) continue;
-          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc, 0, 0});
+          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc, 0, 0, 0});
         }
         if (s->staged_ok)
           for (int kb : {16, 32, 64, 128}) {
             if (slice_set(s, kb).count <= 0) continue;
             for (int v : {2, 4, 8})
-              if (staged_vec_ok(B, S.p.x_dtype, v)) plans.push_back({0, v, 0, dc, 1, kb});
+              if (staged_vec_ok(B, S.p.x_dtype, v)) plans.push_back({0, v, 0, dc, 1, kb, 0});
           }
       }
     }
-  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem, S.step_staged, slice_kb(s)};
+  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem, S.step_staged, slice_kb(s), S.step_c16};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
@@ -1339,6 +1362,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
       S.step_wide = pl.wide;
       s->disc_smem = pl.disc_smem;
       S.step_staged = pl.staged;
+      S.step_c16 = pl.c16;
       if (pl.staged) use_slices(s, slice_set(s, pl.slice_kb));
       if (err == cudaSuccess) err = enqueue_tick(s);  // untimed first tick
       if (err == cudaSuccess) err = cudaEventRecord(e0, s->work);
@@ -1368,6 +1392,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     S.step_wide = pl.wide;
     s->disc_smem = pl.disc_smem;
     S.step_staged = pl.staged;
+    S.step_c16 = pl.c16;
     if (pl.slice_kb > 0) use_slices(s, slice_set(s, pl.slice_kb));
   };
   if (err != cudaSuccess) {
@@ -1382,7 +1407,8 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
   if (plan_out) {
     const bool stg = chosen.step_smem == 0 && chosen.staged;
     *plan_out = (chosen.step_smem > 0 ? 1 : 0) | (chosen.disc_smem > 0 ? 2 : 0) | (chosen.wide ? 4 : 0) |
-                (stg ? 8 : 0) | (chosen.vec << 4) | ((stg ? chosen.slice_kb : 0) << 8);
+                (stg ? 8 : 0) | (chosen.vec << 4) | ((stg ? chosen.slice_kb : 0) << 8) |
+                ((chosen.step_smem > 0 && chosen.c16) ? (1 << 16) : 0);
   }
   if (best_ms_per_tick) *best_ms_per_tick = best / ticks;
   return MQO_OK;

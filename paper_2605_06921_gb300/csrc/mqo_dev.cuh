@@ -119,6 +119,7 @@ struct GraphDev {
   int64_t nnz;
   const int32_t* row_ptr;   // n+1
   const int32_t* col;       // nnz, global ids
+  const uint16_t* col16;    // nnz, member-local ids (every member graph below 65536 nodes), else nullptr
   const int8_t* w;          // nnz or nullptr
   const int32_t* node_off;  // num_graphs+1
   const int32_t* dmax;      // num_graphs
@@ -134,6 +135,7 @@ struct SolverDev {
   int32_t R;        // counter replicas per trajectory (item i adds into replica i % R)
   int32_t step_vec; // trajectories per lane of the global-memory step kernel (0: B/32 or 1)
   int32_t step_wide; // shared-memory step kernel with 16-byte lanes
+  int32_t step_c16;  // shared-memory step kernel reads the 16-bit member-local column indices
   int32_t split;    // CTAs per item of the node-parallel kernels (several when there are few items)
   int32_t step_staged;  // 1: staged-gather step kernel (when the shared-memory one is not used)
   const Slice* slices;  // its slices, their count, and the most rows / CSR entries of one slice

@@ -41,6 +41,8 @@ cudaError_t launch_any_pending(const SolverDev& S, int32_t* out, cudaStream_t st
 cudaError_t launch_validate_csr(const int32_t* rp, const int32_t* col, const int8_t* w, const int32_t* node_off,
                                 int32_t G, int32_t n, int32_t* bad_row, int sms, cudaStream_t stream);
 cudaError_t launch_pool_ctrl(const SolverDev& S, cudaStream_t stream);
+// 16-bit member-local copies of the column indices (every member graph below 65536 nodes)
+cudaError_t launch_col16(const GraphDev& g, uint16_t* col16, cudaStream_t stream);
 cudaError_t launch_pool_apply(const SolverDev& S, cudaStream_t stream);
 
 // graph-level kernels (autograd path)

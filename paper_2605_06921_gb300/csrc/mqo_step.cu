@@ -90,6 +90,9 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   const float lo = MIS ? 0.0f : -1.0f;
   const bool weighted = !MIS && a.g.w != nullptr;
   const int32_t* __restrict__ col = a.g.col;
+  // 16-bit member-local indices where the graph has them: half the index bytes
+  const uint16_t* __restrict__ col16 = a.g.col16;
+  const bool c16 = col16 != nullptr;
   const int8_t* __restrict__ wts = a.g.w;
   constexpr int K = (LPR < 32 / VEC) ? LPR : 32 / VEC;  // lanes sharing one output word
   const unsigned rmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (sub * LPR));
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     for (int c = 0; c < 4; ++c) {
       const int j = rs_ + c * LPR + l;
       const bool jin = j < re_;
-      nxu[c] = jin ? __ldcs(col + j) - off : ng;
+      nxu[c] = jin ? (c16 ? (int)__ldcs(col16 + j) : __ldcs(col + j) - off) : ng;
       nxw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
     }
   };
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
         for (int c = 0; c < 4; ++c) {
           const int j = rs + (ch0 + 4 + c) * LPR + l;
           const bool jin = j < re;
-          nxu[c] = jin ? __ldcs(col + j) - off : ng;
+          nxu[c] = jin ? (c16 ? (int)__ldcs(col16 + j) : __ldcs(col + j) - off) : ng;
           nxw[c] = jin ? (weighted ? (int)wts[j] : 1) : 0;
         }
       }
@@ -344,6 +347,7 @@ cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, c
   a.gflag_step = gflag_step;
   a.tick = S.tick;
   a.slices = S.slices;
+  if (!S.step_c16) a.g.col16 = nullptr;
   a.num_slices = S.num_slices;
   a.slice_rows = S.slice_rows;
   a.slice_cols = S.slice_cols;

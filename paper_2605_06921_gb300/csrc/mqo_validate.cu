@@ -46,6 +46,21 @@ __global__ void __launch_bounds__(256) k_validate_csr(const int32_t* rp, const i
   }
 }
 
+// 16-bit member-local column indices: one CTA per work item (a node range
+// of one member graph), entry j of a row of member graph g gets
+// col[j] - node_off[g]
+__global__ void __launch_bounds__(256) k_col16(const int32_t* rp, const int32_t* col, const int32_t* node_off,
+                                               const Item* items, uint16_t* col16) {
+  const Item it = items[blockIdx.x];
+  const int32_t off = node_off[it.g];
+  for (int32_t j = rp[it.v0] + threadIdx.x; j < rp[it.v1]; j += blockDim.x) col16[j] = (uint16_t)(col[j] - off);
+}
+
+cudaError_t launch_col16(const GraphDev& g, uint16_t* col16, cudaStream_t stream) {
+  if (g.num_items > 0) k_col16<<<g.num_items, 256, 0, stream>>>(g.row_ptr, g.col, g.node_off, g.items, col16);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_validate_csr(const int32_t* rp, const int32_t* col, const int8_t* w, const int32_t* node_off,
                                 int32_t G, int32_t n, int32_t* bad_row, int sms, cudaStream_t stream) {
   const int64_t want = ((int64_t)n * 32 + 255) / 256;

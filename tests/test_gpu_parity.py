@@ -318,6 +318,18 @@ def test_machine_packed_mis(mq, monkeypatch, B, disc):
     _machine(mq, G, p, 400, trace=30)
 
 
+@pytest.mark.parametrize("col16", ["0", "1"])
+def test_shared_memory_step_kernel_index_widths(mq, monkeypatch, col16):
+    """the shared-memory step kernel with 32-bit global and with 16-bit
+    member-local column indices takes the same ticks"""
+    monkeypatch.setenv("MQO_COL16", col16)
+    G = small_batch(4, 60, 120, 0.1, seed=21)
+    p = mq.params(batch=32, x_dtype=1, v_dtype=1, alpha=0.8, momentum=0.45, rho=0.6, t_gs=3, descent_cap=25,
+                  seed=7)
+    s, _ = _machine(mq, G, p, 150)
+    assert s.info()["step_kernel"] == "smem" and s.info()["col16"] == (col16 == "1")
+
+
 @pytest.mark.parametrize("problem", [0, 1])
 def test_autotune_keeps_results(mq, monkeypatch, problem):
     """Autotuning mid-run (every plan tried, state restored) changes no tick of the machine."""
