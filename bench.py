@@ -356,7 +356,9 @@ def profile_traffic(name, variant, sources):
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    # a summary of several kernel variants gives one hash per variant
+    m = re.search(r"source_sha256\[" + re.escape(variant) + r"\]:\s*([0-9a-f]{64})", txt) or \
+        re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
     t = re.search(r"dram_bytes_per_launch\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", txt)
     if not m or not t:
         return None
@@ -1153,8 +1155,9 @@ def autograd_measure(mq, steps, warmup, *, local, rank, dist, cpu, cpu_target_s=
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg / (fwd_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_units", ("mqo_grad.cu", "mqo_dev.cuh")),
-            "kernel": "mqo::k_fb_units (f_B forward; the fused SpMM backward is the same pass plus a write)",
+            "traffic": profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_seg", ("mqo_grad.cu", "mqo_dev.cuh")),
+            "kernel": "mqo::k_fb_seg (f_B forward pass: the segment-stream kernel plus the long-row chunk "
+                      "kernels; the fused SpMM backward is the same pass plus a write)",
             "algorithmic_bytes_per_launch": alg, "forward_ms": fwd_ms,
             "gathered_bytes_per_launch": float(G.nnz) * B * 4,
             "backward_hbm_gbs": fb_kernel_bytes(G, B, True) / (ph["backward"] / steps / 1e3) / 1e9,

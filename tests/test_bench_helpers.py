@@ -56,7 +56,8 @@ def test_committed_profiles_carry_traffic_for_the_current_sources():
     traffic."""
     assert bench.step_kernel_traffic("mis_batched", "bf16", "smem") is not None
     assert bench.step_kernel_traffic("maxcut_regular", "bf16", "global") is not None
-    assert bench.profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_units", ("mqo_grad.cu", "mqo_dev.cuh")) \
+    assert bench.step_kernel_traffic("maxcut_regular", "bf16", "staged") is not None
+    assert bench.profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_seg", ("mqo_grad.cu", "mqo_dev.cuh")) \
         is not None
 
 
