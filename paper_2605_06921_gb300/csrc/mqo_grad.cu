@@ -233,7 +233,7 @@ struct FbBatch {
   int32_t jb;   // first entry of the batch
 };
 
-template <int VEC>
+template <int VEC, bool WEIGHTED>
 __global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
   extern __shared__ __align__(16) unsigned char smem_fb[];
   __shared__ double s_obj[256];
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
     w = 1;
     if (lane < count(x)) {
       c = __ldcs(a.g.col + x.jb + lane);
-      if (a.g.w) w = a.g.w[x.jb + lane];
+      if constexpr (WEIGHTED) w = a.g.w[x.jb + lane];
     }
   };
   auto issue = [&](const FbBatch& x, int32_t c, int slot) {
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
         emit();
         start_row(row + 1);
       }
-      const int w = __shfl_sync(0xffffffffu, w_cur, e);
+      const int w = WEIGHTED ? __shfl_sync(0xffffffffu, w_cur, e) : 1;
       float f[VEC];
       if constexpr (VEC == 1) {
         f[0] = *reinterpret_cast<const float*>(src + e * ROWB);
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
         }
       }
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) acc[q] = w >= 0 ? acc[q] + f[q] : acc[q] - f[q];
+      for (int q = 0; q < VEC; ++q) acc[q] = (!WEIGHTED || w >= 0) ? acc[q] + f[q] : acc[q] - f[q];
     }
     __syncwarp();
     if (cur.jb + PIPE >= cur.d.w) {  // the segment's last batch: its remaining rows
@@ -431,14 +431,19 @@ static cudaError_t launch_fb_vec(const FbArgs& a, int grid, cudaStream_t s) {
       constexpr int ROWB = 32 * VEC * 4;
       constexpr int PIPE = kFbPipeBytes / ROWB < 32 ? kFbPipeBytes / ROWB : 32;
       const size_t smem = (size_t)(kFbPipeThreads / 32) * 2 * PIPE * ROWB;
-      cudaError_t e = cudaFuncSetAttribute(k_fb_seg<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        // one wave: the resident CTAs of every SM (each warp strides over the segments)
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFbPipeThreads, smem);
+        if (e != cudaSuccess) return e;
+        const int pgrid = std::max(1, std::min(grid, per_sm * (grid / 8)));
+        kern<<<pgrid, kFbPipeThreads, smem, s>>>(a);
+        return cudaGetLastError();
+      };
+      const cudaError_t e = a.g.w ? run(k_fb_seg<VEC, true>) : run(k_fb_seg<VEC, false>);
       if (e != cudaSuccess) return e;
-      // one wave: the resident CTAs of every SM (each warp strides over the segments)
-      int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fb_seg<VEC>, kFbPipeThreads, smem);
-      if (e != cudaSuccess) return e;
-      const int pgrid = std::max(1, std::min(grid, per_sm * (grid / 8)));
-      k_fb_seg<VEC><<<pgrid, kFbPipeThreads, smem, s>>>(a);
     }
     if (a.hp.num_chunks > 0) {
       FbArgs c = a;
