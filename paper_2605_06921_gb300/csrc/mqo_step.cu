@@ -23,6 +23,12 @@ namespace mqo {
 // pitch and each row twice, at bytes [0,64) and [64,128); row groups of odd
 // index read the second copy, so the two row groups of a half-warp always
 // use opposite halves of the 32 banks.
+// MIS with bfloat16 x and 4 or 8 trajectories per lane: the checker's
+// neighbour test comes from a running signed max of the gathered bfloat16
+// words (add_bf16_row_max) instead of the neighbours' rounding words
+template <typename TX, int VEC, bool MIS>
+constexpr bool kMaxCheck = MIS && std::is_same<TX, __nv_bfloat16>::value && (VEC == 4 || VEC == 8);
+
 template <typename TX, typename TV, int VEC, int LPR, bool MIS, bool DUP>
 __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -67,7 +73,7 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     }
     for (int i = threadIdx.x; i < pitch / 16; i += blockDim.x)
       *reinterpret_cast<int4*>(smem + (size_t)ng * pitch + i * 16) = make_int4(0, 0, 0, 0);
-    if (MIS) {
+    if (MIS && !kMaxCheck<TX, VEC, MIS>) {
       const uint32_t* zs = Zc + (int64_t)off * BW;
       for (int i = threadIdx.x; i < ng * BW; i += blockDim.x) sZ[i] = zs[i];
       for (int i = threadIdx.x; i < BW; i += blockDim.x) sZ[ng * BW + i] = 0u;
@@ -139,6 +145,9 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
     float acc[VEC];
     int pos[VEC];
     uint32_t orw[4] = {0u, 0u, 0u, 0u};  // OR of the neighbours' words (BW <= 4)
+    uint32_t mx[VEC / 2 > 0 ? VEC / 2 : 1];  // running max of the neighbours' bfloat16 patterns
+#pragma unroll
+    for (int w = 0; w < (VEC / 2 > 0 ? VEC / 2 : 1); ++w) mx[w] = 0u;
 #pragma unroll
     for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
     const int rs = has ? row.y : 0, re = has ? row.z : 0;
@@ -148,7 +157,7 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
       int myo[4], myw[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (MIS)
+        if (MIS && !kMaxCheck<TX, VEC, MIS>)
           for (int w = 0; w < BW; ++w) orw[w] |= sZ[nxu[c] * BW + w];
         myo[c] = nxu[c] * pitch;  // byte offset of the neighbour's row
         myw[c] = nxw[c];
@@ -168,10 +177,14 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
 #pragma unroll
         for (int k = 0; k < LPR; ++k) {
           const int o = __shfl_sync(0xffffffffu, myo[c], k, LPR);
-          if constexpr (MIS && std::is_same<TX, __nv_bfloat16>::value) {
-            // one mixed-precision add per trajectory: the bfloat16 operand is
-            // widened exactly inside the add, which rounds once (RN), so the
-            // sums are those of the widened values added one by one
+          if constexpr (kMaxCheck<TX, VEC, MIS>) {
+            // one mixed-precision add per trajectory (the bfloat16 operand is
+            // widened exactly inside the add, which rounds once, so the sums
+            // are those of the widened values added one by one) and the
+            // checker's "some neighbour in the set" from the same words
+            add_bf16_row_max<VEC>(acc, mx, sXl + o);
+            continue;
+          } else if constexpr (MIS && std::is_same<TX, __nv_bfloat16>::value) {
             add_bf16_row<VEC>(acc, sXl + o);
             continue;
           }
@@ -199,7 +212,13 @@ __global__ void __launch_bounds__(512, 2) k_step_s(StepArgs a) {
       }
     }
     first_group(vb + nwarps * RPW + sub);
-    if (MIS) {
+    if constexpr (kMaxCheck<TX, VEC, MIS>) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const int16_t h = (int16_t)(uint16_t)(mx[e >> 1] >> (16 * (e & 1)));
+        pos[e] = h > (int16_t)0x3F00;  // bfloat16 0.5
+      }
+    } else if (MIS) {
       for (int w = 0; w < BW; ++w)
         for (int o = 1; o < LPR; o <<= 1) orw[w] |= __shfl_xor_sync(0xffffffffu, orw[w], o);
 #pragma unroll
