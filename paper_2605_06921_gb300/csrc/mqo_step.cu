@@ -23,6 +23,34 @@ namespace mqo {
 // pitch and each row twice, at bytes [0,64) and [64,128); row groups of odd
 // index read the second copy, so the two row groups of a half-warp always
 // use opposite halves of the 32 banks.
+// add_bf16_row plus a running maximum of the row's bfloat16 bit patterns read
+// as signed 16-bit integers, one 32-bit word (two trajectories) per mx[]
+// entry.  For bfloat16 values in [0, 1] that order is the order of the
+// values, and -0 (0x8000) reads as the most negative: after a row, half k of
+// mx[w] > 0x3F00 (= 0.5) iff some neighbour of trajectory 2w + k has x > 0.5.
+template <int VEC>
+__device__ __forceinline__ void add_bf16_row_max(float* acc, uint32_t* mx, const unsigned char* p);
+template <>
+__device__ __forceinline__ void add_bf16_row_max<4>(float* acc, uint32_t* mx, const unsigned char* p) {
+  const uint2 r = *reinterpret_cast<const uint2*>(p);
+  add_bf16x2_word(acc[0], acc[1], r.x);
+  add_bf16x2_word(acc[2], acc[3], r.y);
+  mx[0] = __vmaxs2(mx[0], r.x);
+  mx[1] = __vmaxs2(mx[1], r.y);
+}
+template <>
+__device__ __forceinline__ void add_bf16_row_max<8>(float* acc, uint32_t* mx, const unsigned char* p) {
+  const uint4 r = *reinterpret_cast<const uint4*>(p);
+  add_bf16x2_word(acc[0], acc[1], r.x);
+  add_bf16x2_word(acc[2], acc[3], r.y);
+  add_bf16x2_word(acc[4], acc[5], r.z);
+  add_bf16x2_word(acc[6], acc[7], r.w);
+  mx[0] = __vmaxs2(mx[0], r.x);
+  mx[1] = __vmaxs2(mx[1], r.y);
+  mx[2] = __vmaxs2(mx[2], r.z);
+  mx[3] = __vmaxs2(mx[3], r.w);
+}
+
 // MIS with bfloat16 x and 4 or 8 trajectories per lane: the checker's
 // neighbour test comes from a running signed max of the gathered bfloat16
 // words (add_bf16_row_max) instead of the neighbours' rounding words
