@@ -40,20 +40,27 @@ struct NbList {
   int32_t rs, re;
 };
 
-__device__ __forceinline__ void nb_load(NbList& L, const int32_t* s_rp, const int32_t* col, int32_t off, int vl) {
+// member-local id of entry j: the 16-bit copy where the graph has one (half
+// the bytes, and it was just streamed by the step kernel of the same tick)
+__device__ __forceinline__ int32_t local_col(const int32_t* col, const uint16_t* col16, int32_t off, int32_t j) {
+  return col16 ? (int32_t)col16[j] : col[j] - off;
+}
+
+__device__ __forceinline__ void nb_load(NbList& L, const int32_t* s_rp, const int32_t* col, const uint16_t* col16,
+                                        int32_t off, int vl) {
   const int lane = threadIdx.x & 31;
   L.rs = s_rp[vl];
   L.re = s_rp[vl + 1];
 #pragma unroll
   for (int k = 0; k < kNb; ++k) {
     const int32_t j = L.rs + lane + 32 * k;
-    L.u[k] = j < L.re ? __ldcs(col + j) - off : -1;
+    L.u[k] = j < L.re ? local_col(col, col16, off, j) : -1;
   }
 }
 
 // OR over the list (only u < vl if `less`) of word wk of `words`
-__device__ __forceinline__ uint32_t nb_or(const NbList& L, const uint32_t* words, const int32_t* col, int32_t off,
-                                          int Bw, int wk, int vl, bool less) {
+__device__ __forceinline__ uint32_t nb_or(const NbList& L, const uint32_t* words, const int32_t* col,
+                                          const uint16_t* col16, int32_t off, int Bw, int wk, int vl, bool less) {
   const int lane = threadIdx.x & 31;
   uint32_t r = 0u;
 #pragma unroll
@@ -62,7 +69,7 @@ __device__ __forceinline__ uint32_t nb_or(const NbList& L, const uint32_t* words
     if (u >= 0 && (!less || u < vl)) r |= words[u * Bw + wk];
   }
   for (int32_t j = L.rs + 32 * kNb + lane; j < L.re; j += 32) {
-    const int32_t u = col[j] - off;
+    const int32_t u = local_col(col, col16, off, j);
     if (!less || u < vl) r |= words[u * Bw + wk];
   }
 #pragma unroll
@@ -72,7 +79,8 @@ __device__ __forceinline__ uint32_t nb_or(const NbList& L, const uint32_t* words
 
 // bits set in at least one / at least two neighbours' word wk
 __device__ __forceinline__ void nb_once_twice(const NbList& L, const uint32_t* words, const int32_t* col,
-                                              int32_t off, int Bw, int wk, uint32_t& once, uint32_t& twice) {
+                                              const uint16_t* col16, int32_t off, int Bw, int wk, uint32_t& once,
+                                              uint32_t& twice) {
   const int lane = threadIdx.x & 31;
   once = 0u;
   twice = 0u;
@@ -84,7 +92,7 @@ __device__ __forceinline__ void nb_once_twice(const NbList& L, const uint32_t* w
     once |= w;
   }
   for (int32_t j = L.rs + 32 * kNb + lane; j < L.re; j += 32) {
-    const uint32_t w = words[(col[j] - off) * Bw + wk];
+    const uint32_t w = words[local_col(col, col16, off, j) * Bw + wk];
     twice |= once & w;
     once |= w;
   }
@@ -112,6 +120,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
   const int32_t ng = S.g.node_off[g + 1] - off;
   const int32_t* rp = S.g.row_ptr;
   const int32_t* col = S.g.col;
+  const uint16_t* col16 = S.g.col16;
   const int8_t* wts = S.g.w;
   const int nw = ng * Bw;
   uint32_t* sW = reinterpret_cast<uint32_t*>(smem);  // work set
@@ -156,24 +165,24 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
 
   // ---------------- pass A: decisions on the snapshot
   NbList cur, nxt;
-  if ((w_words || w_lane) && vfirst < ng && w_words) nb_load(cur, s_rp, col, off, vfirst);
+  if ((w_words || w_lane) && vfirst < ng && w_words) nb_load(cur, s_rp, col, col16, off, vfirst);
   for (int vl = vfirst; (w_words || w_lane) && vl < ng; vl += vstep) {
-    if (w_words && vl + vstep < ng) nb_load(nxt, s_rp, col, off, vl + vstep);
+    if (w_words && vl + vstep < ng) nb_load(nxt, s_rp, col, col16, off, vl + vstep);
     const int64_t v = off + vl;
     const int32_t rs = s_rp[vl], re = s_rp[vl + 1];
     const int64_t e = v * B + b;
     const bool zv = sbit(sW, vl, Bw, b);
     bool dropv = false, addv = false, flipv = false;
     if (w_drop) {
-      const uint32_t o = nb_or(cur, sW, col, off, Bw, wk, vl, true);
+      const uint32_t o = nb_or(cur, sW, col, col16, off, Bw, wk, vl, true);
       dropv = round == RD_DROP && zv && (o & bit);
     }
     if (w_comp) {
-      const uint32_t o = nb_or(cur, sF, col, off, Bw, wk, vl, true);
+      const uint32_t o = nb_or(cur, sF, col, col16, off, Bw, wk, vl, true);
       addv = round == RD_COMPLETE && sbit(sF, vl, Bw, b) && !(o & bit);
     }
     if (w_flip) {
-      const uint32_t o = nb_or(cur, sA, col, off, Bw, wk, vl, true);
+      const uint32_t o = nb_or(cur, sA, col, col16, off, Bw, wk, vl, true);
       flipv = round == RD_FLIP1 && sbit(sA, vl, Bw, b) && !(o & bit);
     }
     if (w_words) cur = nxt;
@@ -332,9 +341,9 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
 
   // ---------------- pass C: counts of the (new) work set
   const bool act = round != RD_NONE;
-  if (w_act && mis && vfirst < ng) nb_load(cur, s_rp, col, off, vfirst);
+  if (w_act && mis && vfirst < ng) nb_load(cur, s_rp, col, col16, off, vfirst);
   for (int vl = vfirst; w_act && vl < ng; vl += vstep) {
-    if (mis && vl + vstep < ng) nb_load(nxt, s_rp, col, off, vl + vstep);
+    if (mis && vl + vstep < ng) nb_load(nxt, s_rp, col, col16, off, vl + vstep);
     const int64_t v = off + vl;
     const int32_t rs = s_rp[vl], re = s_rp[vl + 1];
     const int64_t e = v * B + b;
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
     if (act) S.owner[e] = 0x7fffffff;
     if (mis) {
       uint32_t once, twice;
-      nb_once_twice(cur, sW, col, off, Bw, wk, once, twice);
+      nb_once_twice(cur, sW, col, col16, off, Bw, wk, once, twice);
       cur = nxt;
       if (act) {
         const bool one = (once & bit) != 0, two = (twice & bit) != 0;
@@ -358,7 +367,7 @@ __global__ void __launch_bounds__(kDgThreads) k_disc_graph(SolverDev S) {
       for (int32_t j = rs; j < re; ++j) {
         const int w = wts ? (int)wts[j] : 1;
         W += w;
-        if (sbit(sW, col[j] - off, Bw, b)) P += w;
+        if (sbit(sW, local_col(col, col16, off, j), Bw, b)) P += w;
       }
       const int as = 2 * P - W;
       acc0 += zv ? (W - P) : P;
