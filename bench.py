@@ -233,7 +233,8 @@ def reference_arm(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": nnz_b / value * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f32 (x {args.x_dtype} / V {args.v_dtype or args.x_dtype} storage, int64 evaluation)", "data": "synthetic",
         "config": {"workload": wl["desc"], "x_dtype": args.x_dtype, "v_dtype": args.v_dtype or args.x_dtype,
                    "nnz": G.nnz, "batch": wl["batch"], "pool_k": args.pool_k, "objective": args.objective},
         "cpu_baseline": dict(base, value=value),
@@ -506,6 +507,12 @@ def measure_solver(mq, G, pkw, xd, vd, steps, warmup, *, autotune=False, clocks_
     vals, _ = s.best(want_bits=False)
     rec["vals"] = vals
     rec.update(best_summary(vals))
+    # descent steps per finished descent over the whole run (a descent ends at
+    # its fixed-point test or at the cap, descent_cap)
+    sts = s.traj_state()
+    nd = sum(t["descents"] for t in sts)
+    rec["mean_descent_steps"] = float(sum(t["steps"] for t in sts)) / nd if nd else None
+    rec["descent_cap"] = pkw["descent_cap"]
     if probe:
         # the FP64 relaxed objective (timed on the device) and, for a few
         # trajectories in a descent, the stored x: the CPU leg states the
@@ -627,7 +634,8 @@ def solver_config_record(mq, name, xd_s, vd_s, steps, warmup, extra_ticks, *, lo
            "stepped_fraction": r["stepped_fraction"], "ms_per_step": r["ms"] / steps,
            "kernel_ms_per_step": {k: v / steps for k, v in r["phase_ms"].items()}, "roofline": roof,
            "clocks": r["clocks"], "gpu_launches": r["launches"], "best_after_ticks": r["ticks_total"]}
-    rec.update({k: r[k] for k in ("best_mean", "best_max", "accepted", "trajectories")})
+    rec.update({k: r[k] for k in ("best_mean", "best_max", "accepted", "trajectories", "mean_descent_steps",
+                                  "descent_cap")})
     if cpu:
         rec["objective_f64"] = objective_error(G, wl, OBJECTIVES[objective], r.get("objective_probe", {}))
         rec["cpu_baseline"] = oracle_single(G, wl, xd, vd, oracle_ticks, OBJECTIVES[objective])

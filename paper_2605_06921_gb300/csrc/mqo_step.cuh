@@ -86,14 +86,17 @@ struct StepArgs {
 // Per-element tail of the step: evaluation of z(x), momentum update,
 // projection, storage rounding.  `nb` is the neighbour information of the
 // element: MIS any-neighbour-in-set flag, MaxCut weighted count P of
-// neighbours with z = 1 (wsum = weighted degree).
-template <typename TX, typename TV>
+// neighbours with z = 1 (wsum = weighted degree).  OBJ >= 0 fixes the MaxCut
+// relaxation at compile time (the f_B instances of the global-memory
+// kernels); -1 reads it from the arguments.
+template <typename TX, typename TV, int OBJ = -1>
 __device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float thr, float lo, TX xin, TV vin,
                                              float acc, int nb, int wsum, bool stepping, TX& xout, TV& vout,
                                              bool& znew, int& c0, int& c1, int& c2) {
   const float x = to_f(xin);
   const float vold = to_f(vin);
   const bool z = x > thr;
+  const int obj = OBJ >= 0 ? OBJ : a.objective;
   if (mis) {
     const bool any = nb != 0;
     c0 += z;
@@ -102,7 +105,7 @@ __device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float 
   } else {
     const int as = 2 * nb - wsum;
     c0 += z ? (wsum - nb) : nb;
-    const bool fixed = cut_fixed(a.objective, a.lambda_, z, as, wsum);
+    const bool fixed = cut_fixed(obj, a.lambda_, z, as, wsum);
     c1 += !fixed;
     const int gn = z ? as : -as;
     c2 += gn > 0;
@@ -112,7 +115,7 @@ __device__ __forceinline__ void step_element(const StepArgs& a, bool mis, float 
     const float tt = a.gamma * acc;
     grad = 1.0f - tt;
   } else {
-    grad = cut_grad(a.objective, a.lambda_, x, acc, wsum);
+    grad = cut_grad(obj, a.lambda_, x, acc, wsum);
   }
   const float m1 = a.momentum * vold;
   const float m2 = a.alpha * grad;

@@ -23,7 +23,7 @@ constexpr int kGather = 4;     // neighbour rows of x in flight per row and row 
 template <int VEC>
 __host__ __device__ constexpr int rows_in_flight() { return VEC >= 4 ? 1 : 2; }
 
-template <typename TX, typename TV, int VEC, bool MIS, bool WEIGHTED>
+template <typename TX, typename TV, int VEC, bool MIS, bool WEIGHTED, int OBJ>
 __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) {
   __shared__ unsigned long long s_cnt[3 * 128];
   __shared__ int32_t s_rp[kItemMaxNodes + 1];
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(512, (VEC >= 8 ? 1 : 2)) k_step_g(StepArgs a) 
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         bool zn;
-        step_element<TX, TV>(a, MIS, thr, lo, xv[r].e[e], vv[r].e[e], acc[r][e], pos[r][e], wsum[r],
+        step_element<TX, TV, OBJ>(a, MIS, thr, lo, xv[r].e[e], vv[r].e[e], acc[r][e], pos[r][e], wsum[r],
                              (stepm >> e) & 1u, xo.e[e], vo.e[e], zn, c0[e], c1[e], c2[e]);
         zbits |= (unsigned)zn << e;
       }
@@ -192,9 +192,12 @@ int default_step_vec(int B, int x_dtype) {
 
 template <typename TX, typename TV, int VEC>
 static cudaError_t launch_vec(const StepArgs& a, int grid, cudaStream_t s) {
-  if (a.problem == PROB_MIS) k_step_g<TX, TV, VEC, true, false><<<grid, 512, 0, s>>>(a);
-  else if (a.g.w) k_step_g<TX, TV, VEC, false, true><<<grid, 512, 0, s>>>(a);
-  else k_step_g<TX, TV, VEC, false, false><<<grid, 512, 0, s>>>(a);
+  const bool fb = a.objective == OBJ_FB;
+  if (a.problem == PROB_MIS) k_step_g<TX, TV, VEC, true, false, -1><<<grid, 512, 0, s>>>(a);
+  else if (a.g.w && fb) k_step_g<TX, TV, VEC, false, true, OBJ_FB><<<grid, 512, 0, s>>>(a);
+  else if (a.g.w) k_step_g<TX, TV, VEC, false, true, -1><<<grid, 512, 0, s>>>(a);
+  else if (fb) k_step_g<TX, TV, VEC, false, false, OBJ_FB><<<grid, 512, 0, s>>>(a);
+  else k_step_g<TX, TV, VEC, false, false, -1><<<grid, 512, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ __device__ __forceinline__ void unpack_row(const unsigned char* p, float* f) {
   }
 }
 
-template <typename TX, typename TV, int VEC, bool MIS, bool WEIGHTED>
+template <typename TX, typename TV, int VEC, bool MIS, bool WEIGHTED, int OBJ>
 __global__ void __launch_bounds__(kStagedThreads, VEC >= 8 ? 2 : 4) k_step_q(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Slice sl = a.slices[blockIdx.x];
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kStagedThreads, VEC >= 8 ? 2 : 4) k_step_q(Ste
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       bool zn;
-      step_element<TX, TV>(a, MIS, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, (stepm >> e) & 1u, xo.e[e],
+      step_element<TX, TV, OBJ>(a, MIS, thr, lo, xv.e[e], vv.e[e], acc[e], pos[e], wsum, (stepm >> e) & 1u, xo.e[e],
                            vo.e[e], zn, c0[e], c1[e], c2[e]);
       zbits |= (unsigned)zn << e;
     }
@@ -180,9 +180,10 @@ static cudaError_t launch_q_vec(const StepArgs& a, size_t smem, cudaStream_t s) 
     kern<<<a.num_slices, kStagedThreads, smem, s>>>(a);
     return cudaGetLastError();
   };
-  if (a.problem == PROB_MIS) return run(k_step_q<TX, TV, VEC, true, false>);
-  if (a.g.w) return run(k_step_q<TX, TV, VEC, false, true>);
-  return run(k_step_q<TX, TV, VEC, false, false>);
+  const bool fb = a.objective == OBJ_FB;
+  if (a.problem == PROB_MIS) return run(k_step_q<TX, TV, VEC, true, false, -1>);
+  if (a.g.w) return fb ? run(k_step_q<TX, TV, VEC, false, true, OBJ_FB>) : run(k_step_q<TX, TV, VEC, false, true, -1>);
+  return fb ? run(k_step_q<TX, TV, VEC, false, false, OBJ_FB>) : run(k_step_q<TX, TV, VEC, false, false, -1>);
 }
 
 bool staged_vec_ok(int B, int x_dtype, int vec) {
