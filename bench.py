@@ -406,14 +406,25 @@ def source_hash(sources) -> str:
     return h.hexdigest()
 
 
-STEP_SOURCES = {"smem": ("mqo_step.cu", "mqo_step.cuh", "mqo_dev.cuh"),
+STEP_SOURCES = {"smem": ("mqo_step.cu", "mqo_step_smem.cuh", "mqo_step.cuh", "mqo_dev.cuh"),
+                "smem_ell": ("mqo_step_ell.cu", "mqo_step_smem.cuh", "mqo_step.cuh", "mqo_dev.cuh"),
                 "global": ("mqo_step_generic.cu", "mqo_step.cuh", "mqo_dev.cuh"),
                 "staged": ("mqo_step_staged.cu", "mqo_step.cuh", "mqo_dev.cuh")}
 
 
+def step_variant(plan):
+    """Profile variant name of a plan: smem, smem_wide (CSR indices),
+    smem_ell, smem_wide_ell (sliced-ELL stream), staged, global."""
+    kern = plan["step_kernel"]
+    return kern + "_ell" if kern.startswith("smem") and plan.get("ell") else kern
+
+
 def step_kernel_traffic(workload, x_dtype, variant):
-    """DRAM bytes per launch of the step kernel variant (smem, smem_wide, staged, global)."""
-    src = STEP_SOURCES[variant if variant in ("global", "staged") else "smem"]
+    """DRAM bytes per launch of the step kernel variant (step_variant)."""
+    if variant in ("global", "staged"):
+        src = STEP_SOURCES[variant]
+    else:
+        src = STEP_SOURCES["smem_ell" if variant.endswith("_ell") else "smem"]
     return profile_traffic(f"step_kernel_{workload}_{x_dtype}", variant, src)
 
 
@@ -578,12 +589,15 @@ def step_roofline(G, B, sx, sv, step_ms, plan, workload, x_dtype, hbm_peak, peak
     """Roofline of the step kernel: algorithmic HBM bytes (CSR once, x and V
     read and written once, rounding words) per launch over its average
     launch time; the shared-memory kernel adds its gather bound."""
-    alg = algorithmic_bytes_per_step(G, B, sx, sv, 2 if plan.get("col16") else 4)
+    # index bytes per CSR entry: 16-bit member-local ids, 32-bit ids, or the
+    # sliced-ELL stream's 32-bit row offsets (its padding not counted)
+    idx = 4 if plan.get("ell") else (2 if plan.get("col16") else 4)
+    alg = algorithmic_bytes_per_step(G, B, sx, sv, idx)
     achieved = alg / (step_ms / 1e3) / 1e9
     hbm = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
            "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
     kern = plan["step_kernel"]
-    traffic = step_kernel_traffic(workload, x_dtype, kern)
+    traffic = step_kernel_traffic(workload, x_dtype, step_variant(plan))
     gathered = float(G.nnz) * B * sx  # neighbour rows of x read per launch
     if kern.startswith("smem"):
         sm_clock = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))

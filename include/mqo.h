@@ -302,7 +302,11 @@ MQO_API mqo_status mqo_traj_state(mqo_solver s, mqo_traj_info* out);
  * gathered rows of x per staged slice (0 without bit 3), bit 16 = the
  * shared-memory step kernel reads 16-bit member-local column indices (kept
  * by the graph when every member graph has fewer than 65535 nodes, 2 bytes
- * per entry of device memory); *smem_bytes = the
+ * per entry of device memory), bit 17 = the shared-memory step kernel reads
+ * its neighbours from the solver's sliced-ELL stream (the rows of a warp
+ * padded to a common length, four neighbour offsets per 16-byte vector;
+ * 2-byte x, MIS with bfloat16 x or unweighted MaxCut; about 4 bytes of
+ * device memory per entry and lane width); *smem_bytes = the
  * shared-memory step kernel's dynamic shared memory per CTA; *items = work
  * items (node ranges of at most 256 nodes); *replicas = counter replicas per
  * trajectory.
@@ -312,14 +316,13 @@ MQO_API mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* 
 
 /*
  * Autotuner of the launch plan: every plan the solver can run (shared-memory
- * or global-memory step kernel, for the latter each choice of trajectories
- * per lane, i.e. lanes per row, and fused or node-parallel discrete passes)
+ * or global-memory step kernel; for the former lane width and neighbour
+ * stream, for the latter each choice of trajectories per lane, i.e. lanes
+ * per row, and of staged slices; fused or node-parallel discrete passes)
  * runs `ticks` machine ticks from the current state; the state is restored
  * after every trial, so tuning changes no result (all plans compute the same
  * ticks bit for bit).  The fastest plan is kept for later ticks.  Writes the
- * plan to *plan (bit 0 shared-memory step, bit 1 fused discrete passes,
- * bit 2 16-byte lanes of the shared-memory step, bits 4.. trajectories per
- * lane of the global-memory step kernel, 0 when bit 0 is set) and its time
+ * plan to *plan (the bits of mqo_solver_info's *step_kernel) and its time
  * per tick in milliseconds to *ms_per_tick
  * (either may be NULL).  Allocates a snapshot of the solver's state for the
  * duration of the call and synchronises.

@@ -51,7 +51,7 @@ def _plan(p):
     else:
         kern = "staged" if p & 8 else "global"
     return {"step_kernel": kern, "discrete_kernel": "graph" if p & 2 else "pairs", "lanes_vec": (p >> 4) & 15,
-            "slice_kb": (p >> 8) & 255, "col16": bool(p & (1 << 16))}
+            "slice_kb": (p >> 8) & 255, "col16": bool(p & (1 << 16)), "ell": bool(p & (1 << 17))}
 
 
 class TrajInfo(C.Structure):

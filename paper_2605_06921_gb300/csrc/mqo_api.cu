@@ -64,6 +64,7 @@ struct mqo_graph_s {
   std::vector<int32_t> h_rp;
   std::vector<int32_t> h_off;
   std::vector<Item> h_items;
+  std::vector<int32_t> h_order;  // rows of every item in processing order
   // f_B kernels: chunk plan of long rows and their scratch
   bool hp_built = false;
   HeavyPlan hp{};
@@ -125,6 +126,20 @@ struct mqo_solver_s {
   };
   std::vector<SliceSet> slice_sets;
   bool staged_ok = false;  // every row's neighbour rows fit the largest capacity
+  // shared-memory step kernel with the sliced-ELL neighbour stream: device
+  // arrays per layout (rows per warp, pitch of the staged x rows), built on
+  // first use
+  struct EllSet {
+    int rpw = 0, pitch = 0;
+    int4* d = nullptr;
+    int2* pos = nullptr;
+    bool ok = false;
+  };
+  std::vector<EllSet> ell_sets;
+  bool ell_ok = false;           // the layout allows the ELL stream
+  bool step_ell = false;         // the current plan uses it
+  const int4* ell = nullptr;     // its arrays for the current lane width
+  const int2* ell_pos = nullptr;
 };
 
 namespace {
@@ -382,6 +397,7 @@ mqo_status build_graph(int32_t G, const int64_t* offs, int64_t n, int64_t nnz, c
   if (e == cudaSuccess) e = cudaMemcpy(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cleanup(fail(MQO_ECUDA, "graph upload: %s", cudaGetErrorString(e)));
+  g->h_order = std::move(order);
   if (on_gpu && nnz > 0) {
     int32_t* d_bad = nullptr;
     if ((st = dalloc(&d_bad, 1, nullptr)) != MQO_OK) return cleanup(st);
@@ -560,6 +576,68 @@ int slice_kb(mqo_solver s) {
   return 0;
 }
 
+// Rows per warp and pitch (bytes between staged rows of x) of the
+// shared-memory step kernel for 2-byte x: 4 trajectories per lane, or 8 with
+// wide lanes; rows of 64 bytes are stored with a 128-byte pitch.
+void ell_shape(int B, bool wide, int* rpw, int* pitch) {
+  const int vec = wide ? 8 : 4;
+  *rpw = 32 / (B / vec);
+  *pitch = B * 2 == 64 ? 128 : B * 2;
+}
+
+// The sliced-ELL arrays for the current batch and lane width, built and
+// uploaded on first use (ok = false if they could not be).  Group table on
+// the host: the rows of every item in groups of rpw positions, each padded
+// to the group's longest row rounded up to 4 entries; vectors on the device.
+mqo_solver_s::EllSet ell_set(mqo_solver s, bool wide) {
+  int rpw = 0, pitch = 0;
+  ell_shape(s->S.B, wide, &rpw, &pitch);
+  for (const auto& es : s->ell_sets)
+    if (es.rpw == rpw && es.pitch == pitch) return es;
+  mqo_solver_s::EllSet es;
+  es.rpw = rpw;
+  es.pitch = pitch;
+  const mqo_graph g = s->g;
+  std::vector<int2> pos((size_t)g->n);
+  int64_t total = 0;
+  for (const Item& it : g->h_items)
+    for (int32_t p0 = it.v0; p0 < it.v1; p0 += rpw) {
+      const int32_t p1 = std::min<int32_t>(p0 + rpw, it.v1);
+      int32_t dmax = 0;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int32_t v = g->h_order[(size_t)p];
+        dmax = std::max<int32_t>(dmax, g->h_rp[(size_t)v + 1] - g->h_rp[(size_t)v]);
+      }
+      const int32_t nvec = (dmax + 3) / 4;
+      for (int32_t p = p0; p < p1; ++p) pos[(size_t)p] = make_int2((int32_t)std::min<int64_t>(total, INT32_MAX), nvec);
+      total += (int64_t)nvec * rpw;
+    }
+  if (total < INT32_MAX && dalloc(&es.d, (size_t)total, &s->allocs) == MQO_OK &&
+      dalloc(&es.pos, (size_t)g->n, &s->allocs) == MQO_OK &&
+      cudaMemcpy(es.pos, pos.data(), sizeof(int2) * (size_t)g->n, cudaMemcpyHostToDevice) == cudaSuccess &&
+      launch_ell_fill(g->dev(), rpw, pitch, es.pos, es.d, s->work) == cudaSuccess &&
+      cudaStreamSynchronize(s->work) == cudaSuccess)
+    es.ok = true;
+  else
+    cudaGetLastError();
+  s->ell_sets.push_back(es);
+  return es;
+}
+
+// selects the CSR (on = false) or the sliced-ELL stream for the current lane
+// width; the CSR one when the ELL arrays are not available
+void use_ell(mqo_solver s, bool on) {
+  s->step_ell = false;
+  s->ell = nullptr;
+  s->ell_pos = nullptr;
+  if (!on || !s->ell_ok) return;
+  const mqo_solver_s::EllSet es = ell_set(s, s->S.step_wide != 0);
+  if (!es.ok) return;
+  s->step_ell = true;
+  s->ell = es.d;
+  s->ell_pos = es.pos;
+}
+
 cudaError_t enqueue_tick(mqo_solver s) {
   cudaError_t e;
   const SolverDev& S = s->S;
@@ -570,7 +648,7 @@ cudaError_t enqueue_tick(mqo_solver s) {
   }
   if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
   if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
-  if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work)) != cudaSuccess) return e;
+  if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work, s->ell, s->ell_pos)) != cudaSuccess) return e;
   if (s->disc_smem > 0) {
     if ((e = launch_disc_graph(S, s->disc_smem, s->work)) != cudaSuccess) return e;
   } else {
@@ -784,6 +862,20 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
     s->S.step_c16 = g->d_col16 != nullptr && !(c16 && strcmp(c16, "0") == 0) ? 1 : 0;
     // MQO_STEP_KERNEL=wide: the shared-memory kernel with 16-byte lanes
     s->S.step_wide = force && strcmp(force, "wide") == 0 && step_wide_possible(B, p->x_dtype) ? 1 : 0;
+    // the sliced-ELL neighbour stream of the shared-memory kernel where the
+    // layout allows it (2-byte x; MIS: bfloat16 x; MaxCut: no weights);
+    // MQO_STEP_ELL=0: the CSR arrays.
+    s->ell_ok = s->step_smem_max > 0 && p->x_dtype != DT_F32 && (B == 32 || B == 64 || B == 128) &&
+                (p->problem == PROB_MIS ? p->x_dtype == DT_BF16 : g->d_w == nullptr);
+    // Default: 16-byte lanes with the ELL stream (the fewest instructions
+    // per gathered byte).  MQO_STEP_ELL=1: the ELL stream with the lanes
+    // MQO_STEP_KERNEL selects (8-byte unless "wide"); MQO_STEP_KERNEL=wide
+    // alone keeps the CSR indices.
+    const char* ellv = getenv("MQO_STEP_ELL");
+    const bool ell_forced = ellv && strcmp(ellv, "1") == 0;
+    const bool ell_off = ellv && strcmp(ellv, "0") == 0;
+    if (!ellv && !force && s->ell_ok && step_wide_possible(B, p->x_dtype)) s->S.step_wide = 1;
+    if (s->step_smem > 0) use_ell(s, ell_forced || (!ell_off && !force));
     // The fused per-graph discrete kernel runs one CTA per member graph, so
     // it is the default only with at least half as many member graphs as
     // SMs; with fewer, the node-parallel passes (several CTAs per item) fill
@@ -922,7 +1014,7 @@ mqo_status mqo_run_timed(mqo_solver s, int64_t nticks, double* phase_ms, int64_t
       if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       if (ek == cudaSuccess) ek = launch_apply(S, s->work);
       if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
-      if (ek == cudaSuccess) ek = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work);
+      if (ek == cudaSuccess) ek = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work, s->ell, s->ell_pos);
       if (ek == cudaSuccess) ek = cudaEventRecordWithFlags(e[i++], s->work, cudaEventRecordExternal);
       for (int pass = 0; pass < 3 && ek == cudaSuccess; ++pass) {
         if (s->disc_smem > 0) {
@@ -976,7 +1068,7 @@ mqo_status mqo_step(mqo_solver s, int32_t nsteps) {
   const SolverDev& S = s->S;
   for (int32_t i = 0; i < nsteps; ++i) {
     CKS(cudaMemsetAsync(s->d_cnt_plain, 0, sizeof(Counters) * (size_t)S.g.num_graphs * S.B * S.R, s->work));
-    CKS(launch_step(S, s->d_cnt_plain, nullptr, nullptr, s->step_smem, s->work));
+    CKS(launch_step(S, s->d_cnt_plain, nullptr, nullptr, s->step_smem, s->work, s->ell, s->ell_pos));
     CKS(launch_tick_end(S, s->work));
   }
   s->host_tick += nsteps;
@@ -1097,7 +1189,8 @@ mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* smem_byt
   if (step_kernel)
     *step_kernel = (s->step_smem > 0 ? 1 : 0) | (s->disc_smem > 0 ? 2 : 0) |
                    (s->step_smem > 0 && s->S.step_wide ? 4 : 0) | (staged ? 8 : 0) | (vec << 4) |
-                   ((staged ? slice_kb(s) : 0) << 8) | ((s->step_smem > 0 && s->S.step_c16) ? (1 << 16) : 0);
+                   ((staged ? slice_kb(s) : 0) << 8) | ((s->step_smem > 0 && s->S.step_c16) ? (1 << 16) : 0) |
+                   ((s->step_smem > 0 && s->step_ell) ? (1 << 17) : 0);
   if (smem_bytes) *smem_bytes = (int64_t)s->step_smem;
   if (items) *items = s->S.g.num_items;
   if (replicas) *replicas = s->S.R;
@@ -1308,6 +1401,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     int staged;   // staged-gather step kernel
     int slice_kb; // its slice capacity
     int c16;      // shared-memory step kernel with 16-bit column indices
+    int ell;      // shared-memory step kernel with the sliced-ELL stream
   };
   std::vector<Plan> plans;
   std::vector<size_t> steps = {0};
@@ -1320,24 +1414,29 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
       if (st > 0) {
         for (int c16 : {0, 1}) {
           if (c16 && !s->g->d_col16) continue;
-          plans.push_back({st, 0, 0, dc, 0, 0, c16});
-          if (wide_ok) plans.push_back({st, 0, 1, dc, 0, 0, c16});
+          plans.push_back({st, 0, 0, dc, 0, 0, c16, 0});
+          if (wide_ok) plans.push_back({st, 0, 1, dc, 0, 0, c16, 0});
+        }
+        if (s->ell_ok) {
+          plans.push_back({st, 0, 0, dc, 0, 0, 0, 1});
+          if (wide_ok) plans.push_back({st, 0, 1, dc, 0, 0, 0, 1});
         }
       } else {
         for (int v : {1, 2, 4, 8}) {
           // 16-byte lanes (8 trajectories) only for 16-bit x and momentum
           if (v == 8 && (S.p.x_dtype == DT_F32 || S.p.v_dtype == DT_F32)) continue;
-          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc, 0, 0, 0});
+          if (B % v == 0 && B / v <= 32 && 32 % (B / v) == 0) plans.push_back({0, v, 0, dc, 0, 0, 0, 0});
         }
         if (s->staged_ok)
           for (int kb : {16, 32, 64, 128}) {
             if (slice_set(s, kb).count <= 0) continue;
             for (int v : {2, 4, 8})
-              if (staged_vec_ok(B, S.p.x_dtype, v)) plans.push_back({0, v, 0, dc, 1, kb, 0});
+              if (staged_vec_ok(B, S.p.x_dtype, v)) plans.push_back({0, v, 0, dc, 1, kb, 0, 0});
           }
       }
     }
-  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem, S.step_staged, slice_kb(s), S.step_c16};
+  const Plan keep{s->step_smem, S.step_vec, S.step_wide, s->disc_smem, S.step_staged, slice_kb(s), S.step_c16,
+                  s->step_ell ? 1 : 0};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
@@ -1364,6 +1463,8 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
       S.step_staged = pl.staged;
       S.step_c16 = pl.c16;
       if (pl.staged) use_slices(s, slice_set(s, pl.slice_kb));
+      use_ell(s, pl.step_smem > 0 && pl.ell);
+      if (pl.ell && !s->step_ell) continue;  // its arrays could not be built
       if (err == cudaSuccess) err = enqueue_tick(s);  // untimed first tick
       if (err == cudaSuccess) err = cudaEventRecord(e0, s->work);
       for (int32_t k = 0; k < ticks && err == cudaSuccess; ++k) err = enqueue_tick(s);
@@ -1394,6 +1495,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     S.step_staged = pl.staged;
     S.step_c16 = pl.c16;
     if (pl.slice_kb > 0) use_slices(s, slice_set(s, pl.slice_kb));
+    use_ell(s, pl.step_smem > 0 && pl.ell);
   };
   if (err != cudaSuccess) {
     apply(keep);
@@ -1408,7 +1510,8 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
     const bool stg = chosen.step_smem == 0 && chosen.staged;
     *plan_out = (chosen.step_smem > 0 ? 1 : 0) | (chosen.disc_smem > 0 ? 2 : 0) | (chosen.wide ? 4 : 0) |
                 (stg ? 8 : 0) | (chosen.vec << 4) | ((stg ? chosen.slice_kb : 0) << 8) |
-                ((chosen.step_smem > 0 && chosen.c16) ? (1 << 16) : 0);
+                ((chosen.step_smem > 0 && chosen.c16) ? (1 << 16) : 0) |
+                ((chosen.step_smem > 0 && chosen.ell) ? (1 << 17) : 0);
   }
   if (best_ms_per_tick) *best_ms_per_tick = best / ticks;
   return MQO_OK;

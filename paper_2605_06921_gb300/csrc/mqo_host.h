@@ -12,8 +12,14 @@ constexpr int kPairThreads = 256;  // pair kernels: (node, trajectory) per threa
 
 enum CtrlMode : int { CTRL_MACHINE = 0, CTRL_LS_BEGIN = 1, CTRL_LS = 2, CTRL_RESET = 3 };
 
+// smem > 0: the shared-memory kernel with that much dynamic shared memory,
+// with the sliced-ELL neighbour stream when `ell` is given (build_ell)
 cudaError_t launch_step(const SolverDev& S, Counters* cnt, const int32_t* act, const int32_t* gflag_step,
-                        size_t smem, cudaStream_t stream);
+                        size_t smem, cudaStream_t stream, const int4* ell = nullptr, const int2* ell_pos = nullptr);
+// the sliced-ELL stream of the shared-memory step kernel (mqo_step_smem.cuh)
+// for `rpw` rows per warp and x rows `pitch` bytes apart, from the group
+// table `pos` (one entry per processing position)
+cudaError_t launch_ell_fill(const GraphDev& g, int rpw, int pitch, const int2* pos, int4* ell, cudaStream_t s);
 bool step_wide_possible(int B, int x_dtype);
 int default_step_vec(int B, int x_dtype);
 bool staged_vec_ok(int B, int x_dtype, int vec);

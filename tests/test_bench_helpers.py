@@ -54,7 +54,7 @@ def test_committed_profiles_carry_traffic_for_the_current_sources():
     """The summaries under profiles/ were captured from the current kernel
     sources (their recorded hash matches), so the bench reports their DRAM
     traffic."""
-    assert bench.step_kernel_traffic("mis_batched", "bf16", "smem") is not None
+    assert bench.step_kernel_traffic("mis_batched", "bf16", "smem_wide_ell") is not None
     assert bench.step_kernel_traffic("maxcut_regular", "bf16", "global") is not None
     assert bench.step_kernel_traffic("maxcut_regular", "bf16", "staged") is not None
     assert bench.profile_traffic("fb_kernel_autograd_powerlaw_f32", "fb_seg", ("mqo_grad.cu", "mqo_dev.cuh")) \

@@ -318,27 +318,74 @@ def test_machine_packed_mis(mq, monkeypatch, B, disc):
     _machine(mq, G, p, 400, trace=30)
 
 
-@pytest.mark.parametrize("col16", ["0", "1"])
-def test_shared_memory_step_kernel_index_widths(mq, monkeypatch, col16):
+@pytest.mark.parametrize("stream", ["csr32", "csr16", "ell"])
+def test_shared_memory_step_kernel_index_streams(mq, monkeypatch, stream):
     """the shared-memory step kernel with 32-bit global and with 16-bit
-    member-local column indices takes the same ticks"""
-    monkeypatch.setenv("MQO_COL16", col16)
+    member-local CSR column indices, and with the sliced-ELL stream, takes
+    the same ticks"""
+    monkeypatch.setenv("MQO_COL16", "1" if stream == "csr16" else "0")
+    monkeypatch.setenv("MQO_STEP_ELL", "1" if stream == "ell" else "0")
     G = small_batch(4, 60, 120, 0.1, seed=21)
     p = mq.params(batch=32, x_dtype=1, v_dtype=1, alpha=0.8, momentum=0.45, rho=0.6, t_gs=3, descent_cap=25,
                   seed=7)
     s, _ = _machine(mq, G, p, 150)
-    assert s.info()["step_kernel"] == "smem" and s.info()["col16"] == (col16 == "1")
+    info = s.info()
+    assert info["step_kernel"] == "smem" and info["col16"] == (stream == "csr16") and info["ell"] == (stream == "ell")
+
+
+def star_batch(leaves=150, seed=0):
+    """a star (one row of `leaves` entries among rows of one entry: its warp
+    group is padded to the hub's length) packed with two ER graphs"""
+    star = mi.from_edges(leaves + 1, np.zeros(leaves, int), np.arange(1, leaves + 1))
+    return mi.pack([mi.erdos_renyi(70, 0.12, seed), star, mi.erdos_renyi(45, 0.2, seed + 1)])
 
 
 @pytest.mark.parametrize("problem", [0, 1])
-def test_autotune_keeps_results(mq, monkeypatch, problem):
-    """Autotuning mid-run (every plan tried, state restored) changes no tick of the machine."""
+@pytest.mark.parametrize("B,xd,vd,wide", [(32, 1, 1, False), (32, 1, 0, False), (64, 1, 1, False),
+                                          (128, 1, 1, False), (32, 1, 1, True), (64, 1, 0, True),
+                                          (128, 1, 1, True), (32, 2, 2, False), (64, 2, 0, True)])
+def test_ell_step_kernel(mq, monkeypatch, problem, B, xd, vd, wide):
+    """the shared-memory step kernel with the sliced-ELL stream for every
+    lane layout (rows per warp 1 to 8), element by element against the
+    oracle's steps and through the machine; MIS with float16 x has no ELL
+    form (its checker reads rounding words) and keeps the CSR indices"""
+    monkeypatch.setenv("MQO_STEP_ELL", "1")
+    if wide:
+        monkeypatch.setenv("MQO_STEP_KERNEL", "wide")
+    p = mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, alpha=0.8 if problem == 0 else 0.05,
+                  momentum=0.5, seed=B + 13)
+    s = _plain_steps(mq, star_batch(seed=B), p, 10)
+    info = s.info()
+    assert info["step_kernel"] == ("smem_wide" if wide else "smem")
+    assert info["ell"] == (problem == 1 or xd == 1)
+    G = small_batch(3, 30, 70, 0.15, seed=B + 3)
+    s, _ = _machine(mq, G, mq.params(problem=problem, batch=B, x_dtype=xd, v_dtype=vd, t_gs=3, descent_cap=20,
+                                     seed=B), 150)
+    assert s.info()["ell"] == (problem == 1 or xd == 1)
+
+
+def test_ell_step_kernel_not_for_weighted_maxcut(mq, monkeypatch):
+    """the ELL stream carries no edge weights: signed MaxCut keeps the CSR
+    indices"""
+    monkeypatch.setenv("MQO_STEP_ELL", "1")
+    G = signed(small_batch(3, 40, 80, 0.1, seed=4), 4)
+    p = mq.params(problem=1, batch=32, x_dtype=1, alpha=0.05, momentum=0.8, seed=2)
+    s = _plain_steps(mq, G, p, 6)
+    assert s.info()["step_kernel"] == "smem" and not s.info()["ell"]
+
+
+@pytest.mark.parametrize("xd", [0, 1])
+@pytest.mark.parametrize("problem", [0, 1])
+def test_autotune_keeps_results(mq, monkeypatch, problem, xd):
+    """Autotuning mid-run (every plan tried, state restored) changes no tick
+    of the machine; with bfloat16 x the candidates include the wide lanes,
+    both CSR index widths and the sliced-ELL stream."""
     monkeypatch.setenv("MQO_DISC_KERNEL", "graph")  # make the fused discrete plan one of the candidates
     G = small_batch(4, 60, 120, 0.1, seed=11)
     if problem == 0:
-        p = mq.params(batch=32, alpha=0.8, momentum=0.45, rho=0.6, t_gs=4, descent_cap=25, seed=3)
+        p = mq.params(batch=32, x_dtype=xd, alpha=0.8, momentum=0.45, rho=0.6, t_gs=4, descent_cap=25, seed=3)
     else:
-        p = mq.params(problem=1, batch=32, alpha=0.05, momentum=0.8, lambda_=0.001, rho=0.8, t_gs=3,
+        p = mq.params(problem=1, batch=32, x_dtype=xd, alpha=0.05, momentum=0.8, lambda_=0.001, rho=0.8, t_gs=3,
                       descent_cap=40, init_kind=1, sigma=0.2, seed=3)
     _machine(mq, G, p, 200, trace=0, tune_at=60)
 
