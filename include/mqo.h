@@ -352,7 +352,9 @@ MQO_API mqo_status mqo_objective_f64(mqo_solver s, double* out);
  * Forward of f_B for a float32 block X (device, n*B node-major) of a graph
  * (the whole packed node range): obj[b] = -lambda sum_v x_vb
  * - sum_v x_vb (A x_b)_v in double (device double[B]).  Rows of degree above
- * an internal split are accumulated in chunks (fixed order).  B in [1,256].
+ * an internal split are accumulated in chunks (fixed order).  B a power of
+ * two in [1,256]; for B >= 32, X must be 16-byte aligned (rows are read in
+ * 16-byte pieces), else MQO_EINVAL and nothing is launched.
  */
 MQO_API mqo_status mqo_fb_forward(mqo_graph g, const float* X, int32_t B, float lambda_, double* obj, void* cuda_stream);
 
@@ -360,7 +362,8 @@ MQO_API mqo_status mqo_fb_forward(mqo_graph g, const float* X, int32_t B, float 
  * Backward of f_B (gradient, Thm 3.6 proof: grad f_B = -lambda 1 - 2 A x):
  * G[v*B+b] = gout[b] * (-lambda - 2 (A X)_{vb}), float32, device arrays;
  * gout may be NULL (taken as 1).  Uses library-owned scratch for the
- * chunk partial sums of high-degree rows.
+ * chunk partial sums of high-degree rows.  B and the alignment of X as for
+ * mqo_fb_forward.
  */
 MQO_API mqo_status mqo_spmm_grad(mqo_graph g, const float* X, const float* gout, float* G, int32_t B, float lambda_,
                          void* cuda_stream);

@@ -1317,6 +1317,8 @@ mqo_status mqo_objective_f64(mqo_solver s, double* out) {
 mqo_status mqo_fb_forward(mqo_graph g, const float* X, int32_t B, float lambda_, double* obj, void* cuda_stream) {
   if (!g || !X || !obj) return fail(MQO_EINVAL, "null argument");
   if (B < 1 || B > 256 || (B & (B - 1))) return fail(MQO_EINVAL, "B=%d must be a power of two in [1,256]", B);
+  // B >= 32: rows of X are read in 16-byte pieces
+  if (B >= 32 && ((uintptr_t)X & 15u) != 0) return fail(MQO_EINVAL, "X must be 16-byte aligned for B >= 32");
   mqo_status st = build_heavy_plan(g);
   if (st != MQO_OK) return st;
   const size_t need = (size_t)g->hp.num_chunks * B;
@@ -1338,6 +1340,8 @@ mqo_status mqo_spmm_grad(mqo_graph g, const float* X, const float* gout, float* 
                          void* cuda_stream) {
   if (!g || !X || !G) return fail(MQO_EINVAL, "null argument");
   if (B < 1 || B > 256 || (B & (B - 1))) return fail(MQO_EINVAL, "B=%d must be a power of two in [1,256]", B);
+  // B >= 32: rows of X are read in 16-byte pieces
+  if (B >= 32 && ((uintptr_t)X & 15u) != 0) return fail(MQO_EINVAL, "X must be 16-byte aligned for B >= 32");
   mqo_status st = build_heavy_plan(g);
   if (st != MQO_OK) return st;
   const size_t need = (size_t)g->hp.num_chunks * B;

@@ -164,3 +164,16 @@ def test_pipelined_kernel_equals_unit_kernel_and_oracle(mq, monkeypatch, B, sign
         assert np.all(np.abs(gh[:, b] - want) <= 1e-5 * go[b] * (lam + 2 * absum) + 1e-7), b
         wobj = oracle.objective_f64(og, oracle.MAXCUT, 0.0, lam, xb)
         assert obj[b] == pytest.approx(wobj, rel=2e-6, abs=1e-3), b
+
+
+def test_misaligned_block_is_rejected(mq):
+    """B >= 32 reads rows of X in 16-byte pieces: a pointer off that
+    boundary is an argument error (nothing launched), not a fault."""
+    G = power_law_with_hub(2000, 600, seed=3)
+    g = mq.Graph(G)
+    buf = torch.zeros(G.n * 32 + 1, device="cuda")
+    X = buf[1:].view(G.n, 32)
+    with pytest.raises(Exception, match="16-byte aligned"):
+        mq.fb_forward(g, X, 0.001)
+    with pytest.raises(Exception, match="16-byte aligned"):
+        mq.spmm_grad(g, X, 0.001)
