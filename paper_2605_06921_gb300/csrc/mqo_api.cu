@@ -102,6 +102,9 @@ struct mqo_solver_s {
   cudaStream_t user = nullptr;
   cudaStream_t work = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // second branch of a tick: the fused discrete kernel beside the step
+  cudaStream_t work2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gx1 = nullptr, gx16 = nullptr;
   bool poisoned = false;
   size_t step_smem = 0;  // > 0: shared-memory step kernel with this much dynamic smem
@@ -638,6 +641,13 @@ void use_ell(mqo_solver s, bool on) {
   s->ell_pos = es.pos;
 }
 
+// MQO_SERIAL_TICK=1: the step and the discrete kernels one after the other
+// (read at every enqueue, so that a test can compare the two orders)
+bool serial_tick() {
+  const char* e = getenv("MQO_SERIAL_TICK");
+  return e && strcmp(e, "1") == 0;
+}
+
 cudaError_t enqueue_tick(mqo_solver s) {
   cudaError_t e;
   const SolverDev& S = s->S;
@@ -648,6 +658,21 @@ cudaError_t enqueue_tick(mqo_solver s) {
   }
   if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
   if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
+  if (s->disc_smem > 0 && s->work2 && !serial_tick()) {
+    // The step (x, V, rounding words; counters of stepping trajectories) and
+    // the fused discrete kernel (work, auxiliary and free bit sets; counters
+    // of trajectories in a round, integer atomics) touch disjoint state and
+    // both follow k_apply: two branches, so that step CTAs fill the SMs the
+    // discrete kernel's tail leaves idle.
+    if ((e = cudaEventRecord(s->ev_fork, s->work)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s->work2, s->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_disc_graph(S, s->disc_smem, s->work2)) != cudaSuccess) return e;
+    if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work, s->ell, s->ell_pos)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(s->ev_join, s->work2)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s->work, s->ev_join, 0)) != cudaSuccess) return e;
+    return launch_tick_end(S, s->work);
+  }
   if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work, s->ell, s->ell_pos)) != cudaSuccess) return e;
   if (s->disc_smem > 0) {
     if ((e = launch_disc_graph(S, s->disc_smem, s->work)) != cudaSuccess) return e;
@@ -781,7 +806,10 @@ mqo_status mqo_solver_create(mqo_graph g, const mqo_params* p, void* cuda_stream
   };
   if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->work2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(MQO_ECUDA, "stream/event creation failed"));
   SolverDev& S = s->S;
   S.g = g->dev();
@@ -941,6 +969,9 @@ mqo_status mqo_solver_destroy(mqo_solver s) {
   if (s->h_pending) cudaFreeHost(s->h_pending);
   if (s->ev_in) cudaEventDestroy(s->ev_in);
   if (s->ev_out) cudaEventDestroy(s->ev_out);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->work2) cudaStreamDestroy(s->work2);
   if (s->work) cudaStreamDestroy(s->work);
   delete s;
   return MQO_OK;
