@@ -658,15 +658,20 @@ cudaError_t enqueue_tick(mqo_solver s) {
   }
   if ((e = launch_ctrl(S, CTRL_MACHINE, nullptr, s->work)) != cudaSuccess) return e;
   if ((e = launch_apply(S, s->work)) != cudaSuccess) return e;
-  if (s->disc_smem > 0 && s->work2 && !serial_tick()) {
+  if (s->work2 && !serial_tick()) {
     // The step (x, V, rounding words; counters of stepping trajectories) and
-    // the fused discrete kernel (work, auxiliary and free bit sets; counters
-    // of trajectories in a round, integer atomics) touch disjoint state and
-    // both follow k_apply: two branches, so that step CTAs fill the SMs the
-    // discrete kernel's tail leaves idle.
+    // the discrete passes (work, auxiliary, free and drop bit sets and the
+    // move arrays; counters of trajectories in a round, integer atomics)
+    // touch disjoint state and both follow k_apply: two branches, so that
+    // step CTAs fill the SMs the discrete kernels leave idle.
     if ((e = cudaEventRecord(s->ev_fork, s->work)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s->work2, s->ev_fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_disc_graph(S, s->disc_smem, s->work2)) != cudaSuccess) return e;
+    if (s->disc_smem > 0) {
+      if ((e = launch_disc_graph(S, s->disc_smem, s->work2)) != cudaSuccess) return e;
+    } else {
+      for (int pass = 0; pass < 3; ++pass)
+        if ((e = launch_disc(S, pass, s->work2)) != cudaSuccess) return e;
+    }
     if ((e = launch_step(S, S.cnt, S.act, S.gflag + 2 * G, s->step_smem, s->work, s->ell, s->ell_pos)) != cudaSuccess)
       return e;
     if ((e = cudaEventRecord(s->ev_join, s->work2)) != cudaSuccess) return e;

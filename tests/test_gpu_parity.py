@@ -318,18 +318,19 @@ def test_machine_packed_mis(mq, monkeypatch, B, disc):
     _machine(mq, G, p, 400, trace=30)
 
 
+@pytest.mark.parametrize("disc", ["graph", "pairs"])
 @pytest.mark.parametrize("serial", ["0", "1"])
-def test_step_and_discrete_branches_take_the_same_ticks(mq, monkeypatch, serial):
-    """The step and the fused discrete kernel run as two branches of a tick
-    (default) or one after the other (MQO_SERIAL_TICK=1): the machine takes
-    the oracle's ticks either way."""
-    monkeypatch.setenv("MQO_DISC_KERNEL", "graph")
+def test_step_and_discrete_branches_take_the_same_ticks(mq, monkeypatch, serial, disc):
+    """The step and the discrete kernels (fused, or the node-parallel passes)
+    run as two branches of a tick (default) or one after the other
+    (MQO_SERIAL_TICK=1): the machine takes the oracle's ticks either way."""
+    monkeypatch.setenv("MQO_DISC_KERNEL", disc)
     monkeypatch.setenv("MQO_SERIAL_TICK", serial)
     G = small_batch(6, 40, 90, 0.15, seed=31)
     p = mq.params(batch=32, x_dtype=1, v_dtype=1, alpha=0.8, momentum=0.45, rho=0.6, t_gs=3, descent_cap=20,
                   seed=13)
     s, _ = _machine(mq, G, p, 300)
-    assert s.info()["discrete_kernel"] == "graph"
+    assert s.info()["discrete_kernel"] == disc
 
 
 @pytest.mark.parametrize("stream", ["csr32", "csr16", "ell"])
