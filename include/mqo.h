@@ -321,7 +321,8 @@ MQO_API mqo_status mqo_solver_info(mqo_solver s, int32_t* step_kernel, int64_t* 
  * per row, and of staged slices; fused or node-parallel discrete passes)
  * runs `ticks` machine ticks from the current state; the state is restored
  * after every trial, so tuning changes no result (all plans compute the same
- * ticks bit for bit).  The fastest plan is kept for later ticks.  Writes the
+ * ticks bit for bit).  The current plan is timed first; another replaces it
+ * only if more than 3 % faster.  The chosen plan is kept for later ticks.  Writes the
  * plan to *plan (the bits of mqo_solver_info's *step_kernel) and its time
  * per tick in milliseconds to *ms_per_tick
  * (either may be NULL).  Allocates a snapshot of the solver's state for the

@@ -1480,6 +1480,12 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  // the current plan is timed first and stays unless another is faster by
+  // more than kTuneMargin: a few ticks cannot see kernels that have no work
+  // yet (early in a run no trajectory is in a discrete round), and noise
+  // alone should not move the plan
+  constexpr double kTuneMargin = 0.03;
+  plans.insert(plans.begin(), keep);
   double best = 1e300;
   Plan chosen = keep;
   {
@@ -1512,7 +1518,7 @@ mqo_status mqo_autotune(mqo_solver s, int32_t ticks, int32_t* plan_out, double* 
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.0f;
       if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-      if (err == cudaSuccess && ms < best) {
+      if (err == cudaSuccess && (best == 1e300 || ms < best * (1.0 - kTuneMargin))) {
         best = ms;
         chosen = pl;
       }
