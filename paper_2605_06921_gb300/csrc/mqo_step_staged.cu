@@ -14,9 +14,9 @@
 //      all at once: one slice keeps tens of kilobytes of gathers in flight,
 //      and several resident CTAs overlap one slice's gathers with another's
 //      arithmetic;
-//   3. waits, then every row group sums its row's neighbours in CSR order
-//      from shared memory (same float32 sums as the other step kernels) and
-//      runs the step tail.
+//   3. waits, then the row groups of a warp sum their rows' neighbours in
+//      CSR order from shared memory, in lockstep over the warp's longest row
+//      (same float32 sums as the other step kernels), and run the step tail.
 // Requirements (checked on the host): a row of x and a row of V are
 // multiples of 16 bytes, and every row's neighbours fit in one slice.
 #include "mqo_step.cuh"
@@ -38,6 +38,30 @@ __device__ __forceinline__ void unpack_row(const unsigned char* p, float* f) {
     load_unpack<T, VEC>(p, f);
   }
 }
+
+// (a, b) += the two 16-bit elements of word w, one mixed-precision add each
+// (sm_100 family: the 16-bit operand is widened exactly inside the add, which
+// rounds once, so the sums equal widening first and adding in float32)
+template <typename TX>
+__device__ __forceinline__ void add_x16x2_word(float& a, float& b, uint32_t w);
+template <>
+__device__ __forceinline__ void add_x16x2_word<__nv_bfloat16>(float& a, float& b, uint32_t w) {
+  add_bf16x2_word(a, b, w);
+}
+template <>
+__device__ __forceinline__ void add_x16x2_word<__half>(float& a, float& b, uint32_t w) {
+  asm("{\n\t.reg .b16 lo, hi;\n\t"
+      "mov.b32 {lo, hi}, %2;\n\t"
+      "add.rn.f32.f16 %0, lo, %0;\n\t"
+      "add.rn.f32.f16 %1, hi, %1;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "r"(w));
+}
+// the 16-bit pattern of 0.5: for values in [0, 1] the patterns read as
+// signed 16-bit integers order like the values (-0 reads as negative), so
+// "some neighbour has x > 0.5" is "the running max of the patterns > it"
+template <typename TX>
+constexpr int16_t kHalfPattern = std::is_same<TX, __half>::value ? (int16_t)0x3800 : (int16_t)0x3F00;
 
 template <typename TX, typename TV, int VEC, bool MIS, bool WEIGHTED, int OBJ>
 __global__ void __launch_bounds__(kStagedThreads, VEC >= 8 ? 2 : 4) k_step_q(StepArgs a) {
@@ -118,39 +142,90 @@ __global__ void __launch_bounds__(kStagedThreads, VEC >= 8 ? 2 : 4) k_step_q(Ste
   const float lo = MIS ? 0.0f : -1.0f;
   const int K = (lpr < 32 / VEC) ? lpr : 32 / VEC;  // lanes sharing one output bit word
   const unsigned rmask = lpr == 32 ? 0xffffffffu : (((1u << lpr) - 1u) << (sub * lpr));
+  // a zero row of x for the padded steps of lockstep rows (rows of x are at
+  // most B = 256 values of 4 bytes)
+  __shared__ __align__(16) unsigned char s_zero[1024];
+  for (int i = tid; i < 1024 / 16; i += nt) reinterpret_cast<int4*>(s_zero)[i] = make_int4(0, 0, 0, 0);
   cp_async_wait_all();
   __syncthreads();
 
-  // 3. one row per row group at a time, neighbours in CSR order
-  for (int vr = warp * rpw + sub; vr < nrows; vr += nwarps * rpw) {
-    const int rs = s_rp[vr], re = s_rp[vr + 1];
-    const Pack<TX, VEC> xv = *reinterpret_cast<const Pack<TX, VEC>*>(s_xo + vr * rowx + b0 * (int)sizeof(TX));
-    const Pack<TV, VEC> vv = *reinterpret_cast<const Pack<TV, VEC>*>(s_vo + vr * rowv + b0 * (int)sizeof(TV));
+  // 3. the rows of a warp in lockstep (row group sub takes row vr0 + sub),
+  //    each summing its neighbours in CSR order for as many steps as the
+  //    warp's longest row; a row's steps past its end read the zero row:
+  //    adding +0.0 leaves a float32 sum that is not -0.0 unchanged (and the
+  //    sums are never -0.0), so the sums equal the CSR-order sums and the
+  //    loop has no per-row branches.  MIS with 16-bit x: one mixed-precision
+  //    add per element, and the checker's "some neighbour in the set" from a
+  //    running signed max of the gathered 16-bit words.
+  constexpr bool kMax16 = MIS && sizeof(TX) == 2 && (VEC == 2 || VEC == 4 || VEC == 8);
+  constexpr int NW = VEC / 2 > 0 ? VEC / 2 : 1;  // 32-bit words of a lane's elements
+  const unsigned char* zp = s_zero + b0 * (int)sizeof(TX);
+  for (int vr0 = warp * rpw; vr0 < nrows; vr0 += nwarps * rpw) {
+    const int vr = vr0 + sub;
+    const bool has = vr < nrows;
+    const int vrc = has ? vr : 0;
+    const int rs = has ? s_rp[vr] : 0, re = has ? s_rp[vr + 1] : 0;
+    const int len = re - rs;
+    const int nmax = __reduce_max_sync(0xffffffffu, len);
+    const Pack<TX, VEC> xv = *reinterpret_cast<const Pack<TX, VEC>*>(s_xo + vrc * rowx + b0 * (int)sizeof(TX));
+    const Pack<TV, VEC> vv = *reinterpret_cast<const Pack<TV, VEC>*>(s_vo + vrc * rowv + b0 * (int)sizeof(TV));
     float acc[VEC];
     int pos[VEC];
+    uint32_t mx[NW];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) { acc[e] = 0.0f; pos[e] = 0; }
-    int wsum = WEIGHTED ? 0 : re - rs;
-    const unsigned char* p = s_nb + rs * rowx + b0 * (int)sizeof(TX);
-    for (int j = rs; j < re; ++j, p += rowx) {
-      float f[VEC];
-      unpack_row<TX, VEC>(p, f);
-      if constexpr (WEIGHTED) {
-        const int w = s_w[j];
-        wsum += w;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          acc[e] = w >= 0 ? acc[e] + f[e] : acc[e] - f[e];
-          pos[e] += (f[e] > thr) ? w : 0;
+    for (int w = 0; w < NW; ++w) mx[w] = 0u;
+    int wsum = WEIGHTED ? 0 : len;
+    const unsigned char* p = s_nb + rs * rowx + b0 * (int)sizeof(TX);
+#pragma unroll 4
+    for (int k = 0; k < nmax; ++k) {
+      const bool in = k < len;
+      const unsigned char* q = in ? p + k * rowx : zp;
+      if constexpr (kMax16) {
+        uint32_t wd[NW];
+        if constexpr (VEC == 8) {
+          const uint4 r = *reinterpret_cast<const uint4*>(q);
+          wd[0] = r.x, wd[1] = r.y, wd[2] = r.z, wd[3] = r.w;
+        } else if constexpr (VEC == 4) {
+          const uint2 r = *reinterpret_cast<const uint2*>(q);
+          wd[0] = r.x, wd[1] = r.y;
+        } else {
+          wd[0] = *reinterpret_cast<const uint32_t*>(q);
+        }
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          add_x16x2_word<TX>(acc[2 * w], acc[2 * w + 1], wd[w]);
+          mx[w] = __vmaxs2(mx[w], wd[w]);
         }
       } else {
+        float f[VEC];
+        unpack_row<TX, VEC>(q, f);
+        if constexpr (WEIGHTED) {
+          const int w = in ? (int)s_w[rs + k] : 0;
+          wsum += w;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          acc[e] = acc[e] + f[e];
-          pos[e] += (f[e] > thr);
+          for (int e = 0; e < VEC; ++e) {
+            acc[e] = w >= 0 ? acc[e] + f[e] : acc[e] - f[e];
+            pos[e] += (f[e] > thr) ? w : 0;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            acc[e] = acc[e] + f[e];
+            pos[e] += (f[e] > thr);
+          }
         }
       }
     }
+    if constexpr (kMax16) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const int16_t h = (int16_t)(uint16_t)(mx[e >> 1] >> (16 * (e & 1)));
+        pos[e] = h > kHalfPattern<TX>;
+      }
+    }
+    if (!has) continue;  // the whole row group (its lanes share vr)
     Pack<TX, VEC> xo;
     Pack<TV, VEC> vo;
     unsigned zbits = 0u;
