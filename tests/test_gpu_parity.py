@@ -379,6 +379,30 @@ def test_ell_step_kernel(mq, monkeypatch, problem, B, xd, vd, wide):
     assert s.info()["ell"] == (problem == 1 or xd == 1)
 
 
+@pytest.mark.parametrize("problem", [0, 1])
+@pytest.mark.parametrize("wide", [False, True])
+def test_ell_step_kernel_isolated_nodes(mq, monkeypatch, problem, wide):
+    """member graphs whose last rows (in decreasing-degree order) have no
+    neighbours: their lockstep groups hold no vectors at all"""
+    monkeypatch.setenv("MQO_STEP_ELL", "1")
+    if wide:
+        monkeypatch.setenv("MQO_STEP_KERNEL", "wide")
+    rng = np.random.default_rng(5)
+    parts = []
+    for k in range(3):
+        n, m = 70 + 9 * k, 40
+        u = rng.integers(0, m, 120)
+        v = rng.integers(0, m, 120)
+        keep = u != v
+        parts.append(mi.from_edges(n, u[keep], v[keep]))  # nodes m .. n-1 isolated
+    G = mi.pack(parts)
+    assert (np.diff(G.row_ptr) == 0).sum() >= 90
+    p = mq.params(problem=problem, batch=32, x_dtype=1, alpha=0.8 if problem == 0 else 0.05, momentum=0.5, seed=4)
+    s = _plain_steps(mq, G, p, 8)
+    assert s.info()["ell"] and s.info()["step_kernel"] == ("smem_wide" if wide else "smem")
+    _machine(mq, G, mq.params(problem=problem, batch=32, x_dtype=1, t_gs=3, descent_cap=20, seed=6), 120)
+
+
 def test_ell_step_kernel_not_for_weighted_maxcut(mq, monkeypatch):
     """the ELL stream carries no edge weights: signed MaxCut keeps the CSR
     indices"""
