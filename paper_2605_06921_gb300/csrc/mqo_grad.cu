@@ -366,32 +366,36 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
     __syncwarp();
     const int cnt = count(cur);
     const unsigned char* src = buf + (size_t)slot * PIPE * ROWB + b0 * 4;
-    for (int e = 0; e < cnt; ++e) {
+    for (int e = 0; e < cnt;) {
       const int32_t j = cur.jb + e;
       while (j >= row_end) {  // rows that end before entry j (empty rows too)
         emit();
         start_row(row + 1);
       }
-      const int w = WEIGHTED ? __shfl_sync(0xffffffffu, w_cur, e) : 1;
-      float f[VEC];
-      if constexpr (VEC == 1) {
-        f[0] = *reinterpret_cast<const float*>(src + e * ROWB);
-      } else if constexpr (VEC == 2) {
-        const float2 p = *reinterpret_cast<const float2*>(src + e * ROWB);
-        f[0] = p.x;
-        f[1] = p.y;
-      } else {
-#pragma unroll
-        for (int q = 0; q < VEC; q += 4) {
-          const float4 p = *reinterpret_cast<const float4*>(src + e * ROWB + q * 4);
-          f[q] = p.x;
-          f[q + 1] = p.y;
-          f[q + 2] = p.z;
-          f[q + 3] = p.w;
+      // the entries of this row in the batch, without a row-end test each
+      const int stop = e + min(cnt - e, row_end - j);
+      for (; e < stop; ++e) {
+        const int w = WEIGHTED ? __shfl_sync(0xffffffffu, w_cur, e) : 1;
+        float f[VEC];
+        if constexpr (VEC == 1) {
+          f[0] = *reinterpret_cast<const float*>(src + e * ROWB);
+        } else if constexpr (VEC == 2) {
+          const float2 p = *reinterpret_cast<const float2*>(src + e * ROWB);
+          f[0] = p.x;
+          f[1] = p.y;
+        } else {
+  #pragma unroll
+          for (int q = 0; q < VEC; q += 4) {
+            const float4 p = *reinterpret_cast<const float4*>(src + e * ROWB + q * 4);
+            f[q] = p.x;
+            f[q + 1] = p.y;
+            f[q + 2] = p.z;
+            f[q + 3] = p.w;
+          }
         }
+  #pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = (!WEIGHTED || w >= 0) ? acc[q] + f[q] : acc[q] - f[q];
       }
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) acc[q] = (!WEIGHTED || w >= 0) ? acc[q] + f[q] : acc[q] - f[q];
     }
     __syncwarp();
     if (cur.jb + PIPE >= cur.d.w) {  // the segment's last batch: its remaining rows
