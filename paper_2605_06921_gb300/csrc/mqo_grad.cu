@@ -281,17 +281,22 @@ __global__ void __launch_bounds__(kFbPipeThreads) k_fb_seg(FbArgs a) {
       if constexpr (WEIGHTED) w = a.g.w[x.jb + lane];
     }
   };
+  // a batch is PIPE * PER = 256 pieces of 16 bytes: in step i lane l copies
+  // piece 32i + l (consecutive lanes, consecutive pieces of a row: whole
+  // rows per instruction), entry k / PER's piece k % PER, to byte 16k of the
+  // buffer; eight steps, unrolled
+  static_assert(PIPE * PER == 256, "256 pieces per batch");
   auto issue = [&](const FbBatch& x, int32_t c, int slot) {
-    unsigned char* dst = buf + (size_t)slot * PIPE * ROWB;
-    const int total = count(x) * PER;
-    for (int k0 = 0; k0 < total; k0 += 32) {  // same trip count on every lane
-      const int k = k0 + lane;
-      const int e = min(k / PER, 31);
-      const int piece = k - (k / PER) * PER;
+    unsigned char* dst = buf + (size_t)slot * PIPE * ROWB + 16 * lane;
+    const int cnt = count(x);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = 32 * i + lane;
+      const int e = k / PER;
       const int32_t ue = __shfl_sync(0xffffffffu, c, e);
-      if (k < total)
-        fb_cp_async16(dst + e * ROWB + piece * 16,
-                      reinterpret_cast<const unsigned char*>(a.X + (int64_t)ue * B) + piece * 16);
+      if (e < cnt)
+        fb_cp_async16(dst + 512 * i,
+                      reinterpret_cast<const unsigned char*>(a.X + (int64_t)ue * B) + 16 * (k % PER));
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
