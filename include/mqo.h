@@ -407,6 +407,16 @@ MQO_API mqo_status mqo_pga_momentum_step(float* x, float* v, const float* grad, 
 MQO_API mqo_status mqo_pga_adam_step(float* x, float* m, float* u, const float* grad, int64_t count, float lr, float b1,
                              float b2, float eps, int64_t t, float lo, float hi, void* cuda_stream);
 
+/*
+ * Measured shared-memory load bandwidth of the current device (bytes per
+ * second over all SMs, in GB/s, into host *gbs): two CTAs per SM stream
+ * conflict-free 16-byte loads, `iters` iterations of four loads per thread,
+ * one untimed launch then one timed with CUDA events.  The denominator of
+ * the shared-memory step kernel's roofline (a measurement aid; no part of the
+ * method).  Synchronises; MQO_EINVAL for iters < 1 or a null pointer.
+ */
+MQO_API mqo_status mqo_measure_smem_gbs(int32_t iters, double* gbs);
+
 /* Thread-local message for the last failure on this thread ("" if none). */
 MQO_API const char* mqo_last_error(void);
 

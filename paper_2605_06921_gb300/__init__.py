@@ -113,6 +113,7 @@ _SIGS = {
     "mqo_pga_momentum_step": [_P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, _P],
     "mqo_pga_adam_step": [_P, _P, _P, _P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int64,
                           C.c_float, C.c_float, _P],
+    "mqo_measure_smem_gbs": [C.c_int32, _P],
 }
 
 
@@ -395,6 +396,13 @@ def spmm_grad_static(graph: Graph, X, lambda_: float, gout=None, out=None):
     g = None if gout is None else gout.to(torch.float32).contiguous()
     _check(lib().mqo_spmm_grad_static(graph.handle, _dptr(X), _dptr(g), _dptr(G), B, float(lambda_), _stream()))
     return G
+
+
+def measure_smem_gbs(iters: int = 4096) -> float:
+    """Measured shared-memory load bandwidth of the current device, GB/s."""
+    out = C.c_double(0.0)
+    _check(lib().mqo_measure_smem_gbs(int(iters), C.byref(out)))
+    return out.value
 
 
 def pga_momentum_step(x, v, grad, lr, mu, lo, hi):

@@ -1393,6 +1393,37 @@ mqo_status mqo_spmm_grad(mqo_graph g, const float* X, const float* gout, float* 
   return MQO_OK;
 }
 
+mqo_status mqo_measure_smem_gbs(int32_t iters, double* gbs) {
+  if (!gbs || iters < 1) return fail(MQO_EINVAL, "bad argument");
+  int dev = 0, sms = 0;
+  CKG(cudaGetDevice(&dev));
+  CKG(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = 2 * sms;  // two CTAs per SM
+  uint32_t* sink = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaMalloc(&sink, sizeof(uint32_t) * (size_t)grid);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) err = launch_smem_probe(grid, iters, sink, s);  // untimed
+  if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+  if (err == cudaSuccess) err = launch_smem_probe(grid, iters, sink, s);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (sink) cudaFree(sink);
+  if (err != cudaSuccess) return fail(MQO_ECUDA, "shared-memory probe: %s", cudaGetErrorString(err));
+  if (ms <= 0.0f) return fail(MQO_ECUDA, "shared-memory probe: no elapsed time");
+  const double bytes = (double)grid * smem_probe_threads() * 4.0 * (double)iters * 16.0;
+  *gbs = bytes / (ms * 1e-3) / 1e9;
+  return MQO_OK;
+}
+
 mqo_status mqo_pga_momentum_step(float* x, float* v, const float* grad, int64_t count, float lr, float mu, float lo,
                                  float hi, void* cuda_stream) {
   if (count < 0 || (count > 0 && (!x || !v || !grad))) return fail(MQO_EINVAL, "bad argument");

@@ -69,6 +69,11 @@ struct HeavyPlan {
 };
 constexpr int kFbSegEntries = 512;
 
+// the shared-memory bandwidth probe (mqo_probe.cu): `grid` CTAs of
+// smem_probe_threads() threads, `iters` iterations of four 16-byte loads each
+cudaError_t launch_smem_probe(int grid, int32_t iters, uint32_t* sink, cudaStream_t s);
+int smem_probe_threads();
+
 cudaError_t launch_fb(const GraphDev& g, const HeavyPlan& hp, const float* X, int B, float lambda_,
                       const float* gout, float* G, double* obj, float* scratch, int grid, cudaStream_t stream);
 cudaError_t launch_momentum(float* x, float* v, const float* grad, int64_t n, float lr, float mu, float lo,
