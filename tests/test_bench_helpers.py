@@ -73,3 +73,24 @@ def test_reference_sample_is_the_oracle_on_a_bounded_sample():
         bench._POOLS.clear()
     assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0 and r["single_core_value"] > 0
     assert np.isfinite(r["value"])
+
+
+def test_step_roofline_takes_the_measured_shared_memory_peak():
+    """The shared-memory roofline divides by the probe's measured bandwidth
+    when the bench has one (and says so), else by the derived 128 B/clk/SM
+    figure; the ELL plans name their own profile variant."""
+    G = mi.pack([mi.erdos_renyi(60, 0.2, k) for k in range(2)])
+    plan = {"step_kernel": "smem_wide", "ell": True, "col16": False}
+    assert bench.step_variant(plan) == "smem_wide_ell"
+    assert bench.step_variant({"step_kernel": "smem", "ell": False}) == "smem"
+    assert bench.step_variant({"step_kernel": "staged", "ell": True}) == "staged"
+    clocks = {"sm_mhz": 2000.0}
+    derived = 128.0 * 152 * 2000.0 * 1e6 / 1e9
+    r0 = bench.step_roofline(G, 32, 2, 2, 0.1, plan, "none", "bf16", 6000.0, "measured", clocks, 152, {})
+    assert r0["peak"] == derived and r0["peak_source"] == "derived"
+    r1 = bench.step_roofline(G, 32, 2, 2, 0.1, plan, "none", "bf16", 6000.0, "measured", clocks, 152,
+                             {"smem_probe_gbs": 39000.0})
+    assert r1["peak"] == 39000.0 and r1["peak_source"].startswith("measured") and r1["peak_derived"] == derived
+    assert abs(r1["frac"] * 39000.0 - r0["frac"] * derived) < 1e-6 * derived
+    # ELL index bytes: 4 per entry in the algorithmic HBM bytes
+    assert r1["hbm"]["algorithmic_bytes_per_launch"] == bench.algorithmic_bytes_per_step(G, 32, 2, 2, 4)
